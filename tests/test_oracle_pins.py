@@ -1,0 +1,330 @@
+"""Pins for the FP64 oracle, against things other than itself.
+
+* explicit Pauli matrices (Kronecker products of I, X, Y, Z) -- the
+  definition in Eq. (sre) before the binary encoding;
+* scipy's Sylvester Hadamard matrix for the FWHT (supplement, FWHT section);
+* closed forms (tests/golden/closed_forms.txt) from single-qubit sums,
+  additivity and faithfulness (properties after Eq. (sre));
+* invariants: Parseval/purity, bounds, Clifford invariance, the real /
+  imaginary pattern of X^x Z^z expectations, the Haar mean of Fig. 1(b).
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from paper_2512_24685_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+PX = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+PY = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+PZ = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+PI = np.eye(2, dtype=np.complex128)
+
+
+def kron_list(mats):
+    """Kronecker product with mats[j] acting on qubit j (bit j of the index):
+    the first factor of np.kron is the most significant bit."""
+    out = np.ones((1, 1), dtype=np.complex128)
+    for m in mats:
+        out = np.kron(m, out)
+    return out
+
+
+def rand_state(N, seed, normalise=True):
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(1 << N) + 1j * rng.standard_normal(1 << N)
+    return v / np.linalg.norm(v) if normalise else v
+
+
+def load_golden():
+    rows = {}
+    with open(os.path.join(HERE, "golden", "closed_forms.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, n, val = line.split("--")[0].split()
+            rows[name] = (int(n), float(val))
+    return rows
+
+
+# ---------------------------------------------------------------- definition
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_table_matches_explicit_pauli_matrices(oracle_mod, N):
+    """Every entry <psi|X^x Z^z|psi> of the direct table equals psi^H P psi with
+    P = tensor_j X^{x_j} Z^{z_j} built from 2x2 matrices (Eq. (Pauli_expect))."""
+    psi = rand_state(N, 11 + N, normalise=False)
+    table = oracle_mod.pauli_table(psi)
+    d = 1 << N
+    for x in range(d):
+        for z in range(d):
+            mats = []
+            for j in range(N):
+                m = PI
+                if (x >> j) & 1:
+                    m = m @ PX
+                if (z >> j) & 1:
+                    m = m @ PZ
+                mats.append(m)
+            P = kron_list(mats)
+            ref = np.vdot(psi, P @ psi)
+            assert abs(table[x, z] - ref) < 1e-13 * max(1.0, abs(ref)), (x, z)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+def test_sum4_matches_hermitian_pauli_group(oracle_mod, N):
+    """S over the Hermitian Pauli strings {I,X,Y,Z}^N (Eq. (sre)) equals the
+    oracle's S over X^x Z^z (phases dropped), by both O1 and O2."""
+    psi = rand_state(N, 100 + N, normalise=False)
+    S_ref = 0.0
+    for word in itertools.product([PI, PX, PY, PZ], repeat=N):
+        e = np.vdot(psi, kron_list(word) @ psi)
+        S_ref += abs(e) ** 4
+    assert oracle_mod.sum4_direct(psi) == pytest.approx(S_ref, rel=1e-12)
+    assert oracle_mod.sum4_xorfwht(psi) == pytest.approx(S_ref, rel=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_direct_equals_xorfwht(oracle_mod, N):
+    """O1 (definition) == O2 (Algorithm 1) on random, unnormalised and
+    complex64-rounded states, per shift and in total."""
+    for seed, norm, c64 in [(1, True, False), (2, False, False), (3, True, True)]:
+        psi = rand_state(N, 1000 * N + seed, normalise=norm)
+        if c64:
+            psi = psi.astype(np.complex64)
+        s1, p1 = oracle_mod.sum4_direct(psi, per_x=True)
+        s2, p2 = oracle_mod.sum4_xorfwht(psi, per_x=True)
+        assert s2 == pytest.approx(s1, rel=1e-12)
+        np.testing.assert_allclose(p2, p1, rtol=1e-11, atol=1e-15 * s1)
+        assert oracle_mod.m2(psi, "direct") == pytest.approx(oracle_mod.m2(psi, "xorfwht"), abs=1e-12)
+
+
+def test_xorfwht_range_partition(oracle_mod):
+    """Sum over shift ranges adds up to the full sum (independence over k)."""
+    psi = rand_state(7, 5)
+    full = oracle_mod.sum4_xorfwht(psi)
+    parts = sum(oracle_mod.sum4_xorfwht(psi, a, a + 32) for a in range(0, 128, 32))
+    assert parts == pytest.approx(full, rel=1e-14)
+
+
+# --------------------------------------------------------------------- FWHT
+
+@pytest.mark.parametrize("N", [1, 2, 5, 9])
+def test_fwht_is_sylvester_hadamard(oracle_mod, N):
+    """FWHT(v) = H v with H = H_2^{tensor N} (scipy's Sylvester matrix)."""
+    v = rand_state(N, 7 + N, normalise=False)
+    H = scipy.linalg.hadamard(1 << N).astype(np.float64)
+    np.testing.assert_allclose(oracle_mod.fwht(v), H @ v, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [3, 10])
+def test_fwht_involution_and_parseval(oracle_mod, N):
+    """FWHT(FWHT(v)) = d v (involution of the normalised WHT) and
+    sum |FWHT v|^2 = d sum |v|^2 (Parseval)."""
+    v = rand_state(N, 3, normalise=False)
+    d = 1 << N
+    w = oracle_mod.fwht(v)
+    np.testing.assert_allclose(oracle_mod.fwht(w), d * v, rtol=1e-12, atol=1e-12)
+    assert np.sum(np.abs(w) ** 2) == pytest.approx(d * np.sum(np.abs(v) ** 2), rel=1e-12)
+    np.testing.assert_allclose(oracle_mod.fwht(np.conj(v)), np.conj(w), rtol=1e-13, atol=1e-13)
+
+
+def test_shift_transform_is_table_row(oracle_mod):
+    """One iteration of Algorithm 1 reproduces row x of the Pauli table."""
+    N = 5
+    psi = rand_state(N, 9, normalise=False)
+    table = oracle_mod.pauli_table(psi)
+    for x in (0, 1, 6, 31):
+        np.testing.assert_allclose(oracle_mod.shift_transform(psi, x), table[x], rtol=1e-12, atol=1e-13)
+
+
+# ------------------------------------------------------------- closed forms
+
+def test_golden_closed_forms(oracle_mod):
+    g = load_golden()
+    s = 1 / math.sqrt(2)
+    f = 1 / math.sqrt(3)
+    states = {
+        "zero": W.basis_state(1),
+        "plus": np.array([s, s], dtype=np.complex128),
+        "T": W.qubit_from_bloch((s, s, 0)),
+        "F": W.qubit_from_bloch((f, f, f)),
+    }
+    for n in (2, 3, 4, 5, 6, 8, 10):
+        states[f"T^{n}"] = W.product_of([states["T"]] * n)
+    for n in (2, 4, 7):
+        states[f"plus^{n}"] = W.product_of([states["plus"]] * n)
+    for n in (2, 3, 5):
+        states[f"F^{n}"] = W.product_of([states["F"]] * n)
+    for name, psi in states.items():
+        n, expect = g[name]
+        assert psi.size == 1 << n
+        for method in (["direct", "xorfwht"] if n <= 8 else ["xorfwht"]):
+            assert oracle_mod.m2(psi, method) == pytest.approx(expect, abs=1e-12), (name, method)
+
+
+@pytest.mark.parametrize("N", [1, 3, 6, 9])
+def test_random_product_states_closed_form(oracle_mod, N):
+    """M2 = -sum_q log2((1 + x_q^4 + y_q^4 + z_q^4) / 2) (additivity)."""
+    for seed in range(3):
+        psi, bloch = W.product_state(N, 500 + seed)
+        expect = -np.sum(np.log2((1 + np.sum(bloch ** 4, axis=1)) / 2))
+        assert oracle_mod.m2(psi) == pytest.approx(expect, abs=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 7, 9])
+def test_stabilizer_states_have_zero_magic(oracle_mod, N):
+    """Faithfulness: random Clifford-circuit states have M2 = 0; computational
+    basis states give S = d exactly."""
+    for seed in range(3):
+        psi = W.stabilizer_state(N, 40 + seed)
+        assert abs(oracle_mod.m2(psi)) < 1e-12
+    for t in (0, (1 << N) - 1):
+        assert oracle_mod.sum4_xorfwht(W.basis_state(N, t)) == float(1 << N)
+
+
+# --------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("N", [2, 5, 6])
+def test_purity_parseval(oracle_mod, N):
+    """sum_{x,z} |A|^2 = d n2^2, and per x sum_z |A_x(z)|^2 =
+    d sum_t |psi_{t^x}|^2 |psi_t|^2 (Parseval applied to the shifted product)."""
+    psi = rand_state(N, 77, normalise=False)
+    d = 1 << N
+    table = oracle_mod.pauli_table(psi)
+    p = np.abs(psi) ** 2
+    n2 = p.sum()
+    assert np.sum(np.abs(table) ** 2) == pytest.approx(d * n2 ** 2, rel=1e-12)
+    for x in range(d):
+        t = np.arange(d)
+        assert np.sum(np.abs(table[x]) ** 2) == pytest.approx(d * np.sum(p[t ^ x] * p), rel=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 3, 6, 8])
+def test_bounds(oracle_mod, N):
+    for seed in range(4):
+        m = oracle_mod.m2(rand_state(N, seed))
+        assert -1e-12 <= m <= math.log2(((1 << N) + 1) / 2) + 1e-12
+
+
+def test_real_imaginary_pattern(oracle_mod):
+    """<psi|X^x Z^z|psi> is real when popc(x&z) is even and imaginary when odd
+    (X^x Z^z is Hermitian up to i^{popc(x&z)})."""
+    N = 5
+    psi = rand_state(N, 21)
+    table = oracle_mod.pauli_table(psi)
+    d = 1 << N
+    for x in range(d):
+        for z in range(d):
+            a = table[x, z]
+            if bin(x & z).count("1") % 2 == 0:
+                assert abs(a.imag) < 1e-14
+            else:
+                assert abs(a.real) < 1e-14
+
+
+def _permute_qubits(psi, N, perm):
+    t = np.arange(1 << N)
+    src = np.zeros_like(t)
+    for j in range(N):
+        src |= ((t >> perm[j]) & 1) << j
+    return psi[src]
+
+
+@pytest.mark.parametrize("N", [4, 7])
+def test_clifford_invariance(oracle_mod, N):
+    """M2 is unchanged by qubit permutations, global phase, complex
+    conjugation, layers of single-qubit Cliffords and CNOT layers."""
+    rng = np.random.default_rng(N)
+    psi = rand_state(N, 300 + N)
+    m = oracle_mod.m2(psi)
+    variants = [
+        _permute_qubits(psi, N, rng.permutation(N)),
+        psi * np.exp(0.7j),
+        np.conj(psi),
+    ]
+    phi = psi.copy()
+    for q in range(N):
+        phi = W.apply_1q(phi, N, q, W._CLIFF1[rng.integers(len(W._CLIFF1))])
+    variants.append(phi)
+    phi = psi.copy()
+    for q in range(0, N - 1, 2):
+        phi = W.apply_2q(phi, N, q, W._CNOT)
+    variants.append(phi)
+    for v in variants:
+        assert oracle_mod.m2(v) == pytest.approx(m, abs=1e-12)
+
+
+def test_additivity(oracle_mod):
+    a = rand_state(3, 1)
+    b = rand_state(4, 2)
+    ab = np.kron(b, a)  # a on the low 3 bits, b on the high 4
+    assert oracle_mod.m2(ab) == pytest.approx(oracle_mod.m2(a) + oracle_mod.m2(b), abs=1e-12)
+
+
+def test_non_clifford_gate_changes_magic(oracle_mod):
+    """Sensitivity: a T gate on a |+> qubit adds log2(4/3)."""
+    s = 1 / math.sqrt(2)
+    plus = np.array([s, s], dtype=np.complex128)
+    T = np.diag([1, np.exp(1j * np.pi / 4)])
+    assert oracle_mod.m2(T @ plus) == pytest.approx(math.log2(4 / 3), abs=1e-14)
+
+
+@pytest.mark.parametrize("N", [4, 6])
+def test_haar_mean(oracle_mod, N):
+    """Fig. 1(b): E[S/d] = E[2^{-M2}] = 4/(d+3) for Haar states (the annealed
+    mean), checked within 4 standard errors over 96 states."""
+    vals = np.array([2.0 ** (-oracle_mod.m2(W.haar_state(N, 7000 + i))) for i in range(96)])
+    d = 1 << N
+    sem = vals.std(ddof=1) / math.sqrt(vals.size)
+    assert abs(vals.mean() - 4 / (d + 3)) < 4 * sem
+
+
+def _explicit_pauli(N, x, z):
+    mats = []
+    for j in range(N):
+        m = PI
+        if (x >> j) & 1:
+            m = m @ PX
+        if (z >> j) & 1:
+            m = m @ PZ
+        mats.append(m)
+    return kron_list(mats)
+
+
+def test_planted_mistakes_are_caught(oracle_mod):
+    """Sensitivity of the pins: plausible slips in the product of Algorithm 1
+    (conjugate dropped; the shift taken as t + x mod d instead of t XOR x;
+    Z signs ignored) each move the per-shift sums sum_z |A_x(z)|^4 away from
+    the explicit-Pauli-matrix values, shown with a tiny Python restatement of
+    the loop.  (Dropping the conjugate leaves the *total* S unchanged -- it
+    re-labels the correlation C_x(s) of the supplement's derivation as
+    C_s(x XOR s) -- which is why the per-shift sums and the per-entry table
+    are pinned, not only S.)"""
+    N = 3
+    d = 1 << N
+    psi = rand_state(N, 4242)
+    expect = np.array([sum(abs(np.vdot(psi, _explicit_pauli(N, x, z) @ psi)) ** 4
+                           for z in range(d)) for x in range(d)])
+    H = scipy.linalg.hadamard(d)
+    t = np.arange(d)
+
+    def per_x(prod, signs=True):
+        out = []
+        for x in range(d):
+            g = prod(x)
+            A = H @ g if signs else np.full(d, g.sum())
+            out.append(np.sum(np.abs(A) ** 4))
+        return np.array(out)
+
+    np.testing.assert_allclose(per_x(lambda x: np.conj(psi[t ^ x]) * psi[t]), expect, rtol=1e-12)
+    np.testing.assert_allclose(oracle_mod.sum4_xorfwht(psi, per_x=True)[1], expect, rtol=1e-12)
+    for slip in (per_x(lambda x: psi[t ^ x] * psi[t]),
+                 per_x(lambda x: np.conj(psi[(t + x) % d]) * psi[t]),
+                 per_x(lambda x: np.conj(psi[t ^ x]) * psi[t], signs=False)):
+        assert np.max(np.abs(slip - expect)) > 1e-3 * expect.max()

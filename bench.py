@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark: Pauli terms/s of the exact XOR-FWHT M2 at N = 20 on GB300.
+
+One step = one full M2 evaluation of an N = 20 Haar-random state (complex64,
+FP32 path): all 4^20 = 1.1e12 Pauli strings X^x Z^z, i.e. every row of the
+hot path (norm, XOR-shifted products, FWHT, |A|^4 reduction, FP64 sum, log2).
+The state is resident in HBM before the timed region; the L2 is flushed
+(a 512 MiB write) between timed steps, outside the per-step CUDA events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 is launched with torchrun: every rank evaluates its own state (weak
+scaling, no data-path collective; the barrier and the max over ranks are
+timing only).  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload on the host cores (rank 0 only).
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Pauli terms/s at N=20 within |dM2|<=1e-6 vs FP64; serve p50/p99 latency"
+UNIT = "Pauli terms/s"
+N_QUBITS = 20
+CONFIG_INDEX = 2  # seeds: 1000 * config + state
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--N", type=int, default=N_QUBITS)
+    ap.add_argument("--mode", default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i] == "Active"})
+        pw = [num(r[3]) for r in self.rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+# --------------------------------------------------------------- oracle arm
+
+def cpu_oracle_sample(N: int, seconds: float, seed: int):
+    """Time the FP64 oracle (Algorithm 1, OpenMP over shifts) on a bounded
+    sample of shifts of the same N=20 state.  Returns (terms/s, cores, sample)."""
+    import numpy as np
+
+    import oracle
+    from paper_2512_24685_gb300 import workloads as W
+    psi = W.haar_state(N, seed, np.complex64)
+    cores = oracle.num_threads()
+    d = 1 << N
+    n = max(1, cores)  # calibration: one shift per thread
+    t0 = time.perf_counter()
+    oracle.sum4_xorfwht(psi, 0, n)
+    dt = time.perf_counter() - t0
+    n_big = int(max(cores, min(d, n * max(1.0, seconds / max(dt, 1e-6)))))
+    n_big = max(cores, (n_big // cores) * cores)
+    t0 = time.perf_counter()
+    oracle.sum4_xorfwht(psi, n, n + n_big)
+    dt = time.perf_counter() - t0
+    return n_big * d / dt, cores, f"N={N} Haar state (complex64 widened to FP64), shifts [{n}, {n + n_big}) of {d}: {n_big * d:.3e} Pauli terms in {dt:.1f} s"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    N = args.N
+    d = 1 << N
+    per_step_s = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    import numpy as np
+    from paper_2512_24685_gb300 import workloads as W
+    psi = W.haar_state(N, W.config_seed(CONFIG_INDEX, 0), np.complex64)
+    cores = oracle.num_threads()
+    t0 = time.perf_counter()
+    oracle.sum4_xorfwht(psi, 0, cores)
+    cal = (time.perf_counter() - t0) / cores  # seconds per shift (parallel)
+    n_step = max(cores, int(per_step_s / max(cal, 1e-9)) // cores * cores)
+    x = cores
+    times = []
+    for k in range(args.warmup + args.steps):
+        a = x % d
+        b = min(d, a + n_step)
+        t0 = time.perf_counter()
+        oracle.sum4_xorfwht(psi, a, b)
+        dt = time.perf_counter() - t0
+        x = b
+        if k >= args.warmup:
+            times.append((b - a) * d / dt)
+    value = statistics.mean(times)
+    total = sum(n_step * d / v for v in times)
+    sample = f"each step: {n_step} shifts of the N={N} Haar state ({n_step * d:.3e} Pauli terms), FP64 oracle, {cores} threads"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"N={N} Haar-random state, all 4^{N} Pauli strings (bounded shift sample per step)",
+                   "N": N},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2512_24685_gb300 import binding, workloads as W
+    binding.load_library()
+    N = args.N
+    d = 1 << N
+    terms = float(d) * float(d)
+    psi_np = W.haar_state(N, W.config_seed(CONFIG_INDEX, rank), np.complex64)
+    psi = torch.from_numpy(psi_np).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    plan = binding.Plan(N, "c64", args.mode)
+    plan.set_profiling(True)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        plan.m2(psi)
+    barrier()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+
+    launches0 = plan.launch_count()
+    step_ms, kern_ms = [], []
+    barrier()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.m2_async(psi, out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(plan.last_kernel_ms()[0])
+    barrier()
+    wall = time.perf_counter() - wall0
+    launches = plan.launch_count() - launches0
+    kname = plan.last_kernel_ms()[1]
+    m2_val = out.item()
+    if sampler:
+        time.sleep(0.2)
+        sampler.stop()
+
+    elapsed_s = sum(step_ms) / 1000.0
+    if dist is not None:
+        t = torch.tensor([elapsed_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_s = t.item()
+    value = world * args.steps * terms / elapsed_s
+
+    # ---- end to end through the public host entry point (pinned host buffer)
+    e2e = None
+    if not args.no_e2e:
+        psi_h = torch.from_numpy(psi_np).pin_memory()
+        plan.m2_host(psi_h)
+        barrier()
+        e2e_s = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.m2_host(psi_h)
+            e2e_s += time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = t.item()
+        launches += 0
+        e2e = {"value": world * args.steps * terms / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(psi_h.numel() * psi_h.element_size()),
+               "d2h_bytes_per_step": 32}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = load_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    clocks = sampler.summary() if sampler else {}
+    max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # FP32 ALU roofline: SMs x 128 FP32 lanes x max SM clock (one add / mul /
+    # fma per lane per clock); algorithmic ops per state (2N + 11) 4^N.
+    alg_ops = (2 * N + 11) * terms
+    kern_s = statistics.mean(kern_ms) / 1000.0
+    if args.mode == "fp64":
+        peak_ops = None
+    else:
+        peak_ops = sms * 128 * max_mhz * 1e6
+    achieved = alg_ops / kern_s
+    roof = {
+        "bound": "alu", "kernel": kname,
+        "achieved": achieved / 1e12, "peak": (peak_ops / 1e12) if peak_ops else None,
+        "unit": "TFLOP/s", "frac": (achieved / peak_ops) if peak_ops else None,
+        "traffic": None,
+        "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (sm max); clocks {peak_src}",
+        "alg_ops_per_launch": alg_ops, "kernel_ms": statistics.mean(kern_ms),
+    }
+    if clocks.get("sm_mhz"):
+        roof["frac_at_median_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6)
+
+    cpu = None
+    if not args.no_cpu_baseline and world >= 1:
+        v, cores, sample = cpu_oracle_sample(N, args.cpu_seconds, W.config_seed(CONFIG_INDEX, 0))
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.mode != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"N={N} Haar-random state (complex64), all 4^{N} Pauli strings per step",
+                   "N": N, "states_per_gpu": 1, "mode": args.mode, "l2_flush": "512 MiB write between steps",
+                   "parallelism": f"replicas x{world}"},
+        "m2": m2_val, "states_per_s": world * args.steps / elapsed_s,
+        "gpu_launches": int(launches), "wall_s": wall,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

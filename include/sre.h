@@ -1,0 +1,243 @@
+/*
+ * sre.h -- C ABI of libsre: the second-order stabilizer Renyi entropy M2 of
+ * an N-qubit pure state by the exact XOR-FWHT method, on one NVIDIA GB300
+ * (sm_103a).
+ *
+ * What is computed (paper, "Algebraic Reformulation" and Algorithm 1).
+ * The state |psi> = sum_t phi_t |t>, t in {0,1}^N, is a vector of d = 2^N
+ * complex amplitudes; qubit j is bit j of the index t.  For every X-mask x
+ * and Z-mask z, Eq. (Pauli_expect) gives
+ *     A_x(z) = <psi| X^x Z^z |psi> = sum_t (-1)^{popc(z & t)} conj(phi_{t^x}) phi_t,
+ * i.e. the unnormalised Walsh-Hadamard transform over t of the XOR-shifted
+ * product g_x(t) = conj(phi_{t^x}) phi_t.  Eq. (final1) / Algorithm 1:
+ *     S  = sum_{x,z} |A_x(z)|^4,      M2 = -log2( S / d ),
+ * for a normalised state.  The library does not rescale the caller's
+ * amplitudes: it computes n2 = <psi|psi> in FP64 and returns
+ *     M2 = -log2( S / (d * n2^4) ),
+ * which is the same quantity for the normalised state (S scales as n2^4).
+ * The logarithm is base 2 (Algorithm 1, last step).
+ *
+ * Conventions for every entry point:
+ *  - Device pointers are CUDA device (or managed) addresses on the current
+ *    device; host pointers are ordinary host addresses.
+ *  - State buffers are interleaved complex: (re, im) float pairs for
+ *    SRE_C64, (re, im) double pairs for SRE_C128, d = 2^N entries, 8- or
+ *    16-byte aligned respectively, contiguous.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; entry points marked "synchronous"
+ *    wait for that stream before returning.
+ *  - The caller owns every buffer it passes and keeps it valid until the
+ *    work that reads or writes it has completed on `stream`.
+ *  - A plan owns its device scratch; one plan must not be used from two
+ *    host threads, or on two streams, at the same time.
+ *  - Every function returns an sre_status_t; on error nothing is written to
+ *    the caller's outputs unless stated otherwise.
+ */
+#ifndef SRE_H_
+#define SRE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SRE_API __attribute__((visibility("default")))
+#else
+#define SRE_API
+#endif
+
+#define SRE_MAX_QUBITS 24 /* largest N a plan accepts */
+
+typedef enum {
+    SRE_OK = 0,
+    SRE_EINVAL = 1,       /* bad N, null pointer, bad dtype / mode / range */
+    SRE_EALIGN = 2,       /* misaligned pointer */
+    SRE_EZERO = 3,        /* the state has zero norm */
+    SRE_ENONFINITE = 4,   /* a NaN or Inf amplitude */
+    SRE_ENOMEM = 5,       /* device or host allocation failed */
+    SRE_EBUSY = 6,        /* server admission rejected (HBM budget / queue full) */
+    SRE_ETIMEDOUT = 7,    /* a bounded device-side wait expired */
+    SRE_ECUDA = 8,        /* a CUDA runtime call failed (see sre_last_cuda_error) */
+    SRE_ENOTFOUND = 9,    /* unknown server ticket */
+    SRE_EUNSUPPORTED = 10 /* mode not available for this N / dtype */
+} sre_status_t;
+
+typedef enum {
+    SRE_C64 = 0,  /* interleaved float32 (re, im) */
+    SRE_C128 = 1  /* interleaved float64 (re, im) */
+} sre_dtype_t;
+
+/* Arithmetic used for the product, the transform and the per-element
+ * |A|^4; the cross-shift accumulation, the norm and the final log are FP64
+ * in every mode. */
+typedef enum {
+    SRE_MODE_FP32 = 0,       /* CUDA-core FP32 butterflies */
+    SRE_MODE_BF16_SPLIT = 1, /* tensor-core Hadamard stages, bf16 hi/lo split, FP32 accumulate */
+    SRE_MODE_FP16_SPLIT = 2, /* tensor-core Hadamard stages, fp16 hi/lo split, FP32 accumulate */
+    SRE_MODE_TF32_SPLIT = 3, /* tensor-core Hadamard stages, tf32 hi/lo split, FP32 accumulate */
+    SRE_MODE_FP64 = 4,       /* CUDA-core FP64 everywhere */
+    SRE_MODE_AUTO = -1       /* the plan's tuned default */
+} sre_mode_t;
+
+typedef struct sre_plan_s *sre_plan_t;
+typedef void *sre_stream_t; /* cudaStream_t */
+
+/* Human-readable message for a status (static storage, never NULL). */
+SRE_API const char *sre_status_str(sre_status_t status);
+
+/* Text of the last CUDA error seen by this host thread ("" if none). */
+SRE_API const char *sre_last_cuda_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+SRE_API int sre_version(void);
+
+/*
+ * Create a plan for states of up to N qubits (1 <= N <= SRE_MAX_QUBITS) of
+ * element type `dtype` on the current CUDA device.  The plan allocates its
+ * device scratch here (reduction partials, status words, and for N > 12 the
+ * ring of inter-pass scratch, sized from N and the device's L2).  *out is
+ * set only on SRE_OK.  Errors: SRE_EINVAL (N or dtype out of range, out
+ * NULL), SRE_ENOMEM, SRE_ECUDA.
+ */
+SRE_API sre_status_t sre_plan_create(int N, sre_dtype_t dtype, sre_plan_t *out);
+
+/* Select the arithmetic mode (default SRE_MODE_FP32 for SRE_C64 plans,
+ * SRE_MODE_FP64 for SRE_C128 plans).  SRE_EUNSUPPORTED if the mode is not
+ * built for this plan. */
+SRE_API sre_status_t sre_plan_set_mode(sre_plan_t plan, sre_mode_t mode);
+SRE_API sre_status_t sre_plan_get_mode(sre_plan_t plan, sre_mode_t *mode);
+
+/* Profiling support.  When enabled (enable != 0), the plan records two CUDA
+ * events on the stream around the main transform kernel of each evaluation;
+ * sre_plan_last_kernel_ms waits for the second event and returns the
+ * elapsed milliseconds of the last evaluation's main kernel and its name
+ * (static string).  sre_plan_launch_count returns the number of kernels
+ * the plan has launched since it was created (its own kernels only). */
+SRE_API sre_status_t sre_plan_set_profiling(sre_plan_t plan, int enable);
+SRE_API sre_status_t sre_plan_last_kernel_ms(sre_plan_t plan, double *ms, const char **name);
+SRE_API sre_status_t sre_plan_launch_count(sre_plan_t plan, uint64_t *count);
+
+/* Release the plan and its device memory.  Waits for the plan's work on the
+ * device to finish first.  NULL is accepted. */
+SRE_API sre_status_t sre_plan_destroy(sre_plan_t plan);
+
+/*
+ * M2 of one state (Algorithm 1 over all d shifts), SYNCHRONOUS.
+ * d_state: device buffer of 2^N elements of the plan's dtype, N <= plan N.
+ * m2_host: host double receiving M2.  Waits for `stream`.
+ * Errors: SRE_EINVAL, SRE_EALIGN, SRE_EZERO (n2 == 0), SRE_ENONFINITE
+ * (a NaN/Inf amplitude), SRE_ETIMEDOUT, SRE_ECUDA.
+ */
+SRE_API sre_status_t sre_m2(sre_plan_t plan, const void *d_state, int N, sre_stream_t stream,
+                    double *m2_host);
+
+/*
+ * Asynchronous M2: enqueue the whole computation on `stream` and write M2
+ * to the device double d_m2 (NaN when the state has zero norm or a
+ * non-finite amplitude).  Returns after enqueueing; argument errors are
+ * reported immediately, data errors only through the NaN.
+ */
+SRE_API sre_status_t sre_m2_async(sre_plan_t plan, const void *d_state, int N, sre_stream_t stream,
+                          double *d_m2);
+
+/*
+ * End-to-end M2 from a HOST buffer: copies the 2^N amplitudes host->device
+ * on `stream` (pinned host memory gives an asynchronous copy), computes,
+ * and reads M2 back.  SYNCHRONOUS.  Same errors as sre_m2.
+ */
+SRE_API sre_status_t sre_m2_host(sre_plan_t plan, const void *h_state, int N, sre_stream_t stream,
+                         double *m2_host);
+
+/*
+ * Partial sum over a range of X-masks (the paper's shift k; shifts are
+ * independent, so a state's work splits by shift range):
+ *     d_out[0] = sum_{x in [x_begin, x_end)} sum_z |A_x(z)|^4      (FP64)
+ *     d_out[1] = n2 = <psi|psi>                                    (FP64)
+ * d_out is a device buffer of 2 doubles.  If d_per_x is not NULL it is a
+ * device buffer of (x_end - x_begin) doubles receiving each shift's
+ * sum_z |A_x(z)|^4 (available for N >= 13; SRE_EUNSUPPORTED below).
+ * Asynchronous.  Shards over ranges add up to the full S; M2 follows as
+ * -log2(S / (d n2^4)).  SRE_EINVAL unless 0 <= x_begin < x_end <= 2^N.
+ */
+SRE_API sre_status_t sre_sum4_range(sre_plan_t plan, const void *d_state, int N, uint64_t x_begin,
+                            uint64_t x_end, sre_stream_t stream, double *d_out,
+                            double *d_per_x);
+
+/*
+ * M2 of `count` states of uneven size in one submission (states may have
+ * different N, each <= the plan's N).  d_states: host array of `count`
+ * device pointers; Ns: host array of the N_i; d_m2_out: device array of
+ * `count` doubles (NaN for a zero / non-finite state).  The batch is
+ * executed by persistent kernels walking one work list, and is replayed
+ * from a captured CUDA graph when the same (pointers, Ns) batch is
+ * submitted again.  Asynchronous.  Errors: SRE_EINVAL, SRE_EALIGN,
+ * SRE_ENOMEM, SRE_ECUDA.
+ */
+SRE_API sre_status_t sre_m2_batched(sre_plan_t plan, const void *const *d_states, const int *Ns,
+                            int count, sre_stream_t stream, double *d_m2_out);
+
+/* ----------------------------------------------------------------------- */
+/* Serving: continuous batching of M2 requests of mixed N.                  */
+/* ----------------------------------------------------------------------- */
+
+typedef struct sre_server_s *sre_server_t;
+
+typedef struct {
+    uint64_t hbm_budget_bytes; /* admission limit on resident request bytes */
+    int max_inflight;          /* slots: requests on the device at once */
+    int max_queue;             /* waiting requests before SRE_EBUSY */
+    int max_N;                 /* largest N accepted */
+    sre_mode_t mode;           /* arithmetic for every request */
+    uint64_t wait_limit_ns;    /* bound on every device-side wait */
+    int device;                /* CUDA device ordinal */
+} sre_server_cfg_t;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, rejected, failed;
+    uint64_t inflight, queued;
+    double p50_latency_ms, p99_latency_ms, mean_latency_ms;
+    double states_per_s, pauli_terms_per_s; /* since the first submission */
+    uint64_t resident_bytes, peak_resident_bytes;
+} sre_server_stats_t;
+
+/* Fill cfg with defaults (HBM budget 8 GiB, 32 slots, 4096 queued,
+ * max_N 20, FP32, 5 s wait limit, device 0). */
+SRE_API void sre_server_cfg_default(sre_server_cfg_t *cfg);
+
+/* Start a server: a host scheduler thread plus device streams.  *out set
+ * on SRE_OK.  Errors: SRE_EINVAL, SRE_ENOMEM, SRE_ECUDA. */
+SRE_API sre_status_t sre_server_create(const sre_server_cfg_t *cfg, sre_server_t *out);
+
+/*
+ * Submit one request.  state: interleaved amplitudes of `dtype`, 2^N of
+ * them, in host memory if on_device == 0 or device memory if 1.  The
+ * server copies the state into memory it owns before returning, so the
+ * caller may reuse its buffer at once.  *ticket identifies the request.
+ * Errors: SRE_EINVAL, SRE_EBUSY (queue full, or the request alone exceeds
+ * the HBM budget), SRE_ENOMEM.
+ */
+SRE_API sre_status_t sre_server_submit(sre_server_t srv, const void *state, int on_device, int N,
+                               sre_dtype_t dtype, uint64_t *ticket);
+
+/* Non-blocking poll: *done = 1 and *m2 set once the request finished
+ * (M2 is NaN for a zero / non-finite state); *done = 0 otherwise.  A
+ * finished ticket is forgotten after it has been polled done once.
+ * SRE_ENOTFOUND for an unknown ticket, SRE_ETIMEDOUT if its device wait
+ * expired. */
+SRE_API sre_status_t sre_server_poll(sre_server_t srv, uint64_t ticket, int *done, double *m2);
+
+/* Block until `ticket` is done or timeout_ms elapses (SRE_ETIMEDOUT). */
+SRE_API sre_status_t sre_server_wait(sre_server_t srv, uint64_t ticket, double timeout_ms, double *m2);
+
+SRE_API sre_status_t sre_server_stats(sre_server_t srv, sre_server_stats_t *stats);
+
+/* Stop the scheduler, drain in-flight work, free everything.  NULL ok. */
+SRE_API sre_status_t sre_server_destroy(sre_server_t srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SRE_H_ */

@@ -1,0 +1,296 @@
+// sre_api.cu -- plans and the single-state / range / batched entry points of
+// the libsre C ABI (declared and documented in include/sre.h).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "sre_batched.h"
+#include "sre_internal.h"
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+sre_status_t cuda_fail(cudaError_t e) {
+    g_last_cuda_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return SRE_ENOMEM;
+    return SRE_ECUDA;
+}
+
+int elem_bytes_for_mode(sre_mode_t m) { return m == SRE_MODE_FP64 ? 16 : 8; }
+int dtype_bytes(sre_dtype_t t) { return t == SRE_C128 ? 16 : 8; }
+
+bool mode_supported(sre_mode_t m) {
+    return m == SRE_MODE_FP32 || m == SRE_MODE_FP64 || sre::tc_mode_available(m);
+}
+
+}  // namespace
+
+struct sre_plan_s {
+    int N = 0;
+    sre_dtype_t dtype = SRE_C64;
+    sre_mode_t mode = SRE_MODE_FP32;
+    sre::DeviceInfo dev;
+    sre::Workspace ws;
+    sre::Result *h_result = nullptr;  // pinned
+    void *d_stage = nullptr;          // device copy of a host state (sre_m2_host)
+    size_t d_stage_bytes = 0;
+    long long wait_ns = 5000000000ll;
+    sre::BatchedContext *batched = nullptr;
+    bool profiling = false;
+    unsigned long long extra_launches = 0;  // launches of workspaces that were freed
+};
+
+namespace {
+
+sre_status_t plan_realloc(sre_plan_t p, sre_mode_t mode) {
+    p->extra_launches += p->ws.launches;
+    const bool had_events = p->ws.ev_begin != nullptr;
+    sre::workspace_free(&p->ws);
+    const int eb = elem_bytes_for_mode(mode);
+    cudaError_t e = sre::workspace_alloc(&p->ws, p->dev, p->N, eb, mode);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (had_events) {
+        e = cudaEventCreate(&p->ws.ev_begin);
+        if (e == cudaSuccess) e = cudaEventCreate(&p->ws.ev_end);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (dtype_bytes(p->dtype) != eb) {
+        p->ws.conv_bytes = (size_t)eb << p->N;
+        e = cudaMalloc(&p->ws.conv, p->ws.conv_bytes);
+        if (e != cudaSuccess) {
+            p->ws.conv = nullptr;
+            p->ws.conv_bytes = 0;
+            return cuda_fail(e);
+        }
+    }
+    return SRE_OK;
+}
+
+sre_status_t check_state(sre_plan_t p, const void *ptr, int N) {
+    if (!p || !ptr) return SRE_EINVAL;
+    if (N < 1 || N > p->N) return SRE_EINVAL;
+    if (((uintptr_t)ptr) % dtype_bytes(p->dtype)) return SRE_EALIGN;
+    return SRE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sre_status_str(sre_status_t s) {
+    switch (s) {
+        case SRE_OK: return "ok";
+        case SRE_EINVAL: return "invalid argument (N, pointer, dtype, mode or range)";
+        case SRE_EALIGN: return "misaligned pointer";
+        case SRE_EZERO: return "state has zero norm";
+        case SRE_ENONFINITE: return "state has a NaN or Inf amplitude";
+        case SRE_ENOMEM: return "out of memory";
+        case SRE_EBUSY: return "admission rejected (HBM budget or queue full)";
+        case SRE_ETIMEDOUT: return "bounded device wait expired";
+        case SRE_ECUDA: return "CUDA runtime error";
+        case SRE_ENOTFOUND: return "unknown ticket";
+        case SRE_EUNSUPPORTED: return "mode not available for this plan";
+    }
+    return "unknown status";
+}
+
+const char *sre_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int sre_version(void) { return 10000; }
+
+sre_status_t sre_plan_create(int N, sre_dtype_t dtype, sre_plan_t *out) {
+    if (!out || N < 1 || N > SRE_MAX_QUBITS) return SRE_EINVAL;
+    if (dtype != SRE_C64 && dtype != SRE_C128) return SRE_EINVAL;
+    sre_plan_t p = new (std::nothrow) sre_plan_s();
+    if (!p) return SRE_ENOMEM;
+    p->N = N;
+    p->dtype = dtype;
+    p->mode = dtype == SRE_C128 ? SRE_MODE_FP64 : SRE_MODE_FP32;
+    cudaError_t e = sre::query_device(&p->dev);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e);
+    }
+    sre_status_t s = plan_realloc(p, p->mode);
+    if (s != SRE_OK) {
+        sre::workspace_free(&p->ws);
+        delete p;
+        return s;
+    }
+    e = cudaMallocHost(&p->h_result, sizeof(sre::Result));
+    if (e != cudaSuccess) {
+        sre::workspace_free(&p->ws);
+        delete p;
+        return cuda_fail(e);
+    }
+    *out = p;
+    return SRE_OK;
+}
+
+sre_status_t sre_plan_set_mode(sre_plan_t p, sre_mode_t mode) {
+    if (!p) return SRE_EINVAL;
+    if (mode == SRE_MODE_AUTO) mode = p->dtype == SRE_C128 ? SRE_MODE_FP64 : SRE_MODE_FP32;
+    if ((int)mode < 0 || (int)mode > (int)SRE_MODE_FP64) return SRE_EINVAL;
+    if (!mode_supported(mode)) return SRE_EUNSUPPORTED;
+    if (elem_bytes_for_mode(mode) != elem_bytes_for_mode(p->mode) || !p->ws.result) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e);
+        sre_status_t s = plan_realloc(p, mode);
+        if (s != SRE_OK) return s;
+    }
+    p->mode = mode;
+    return SRE_OK;
+}
+
+sre_status_t sre_plan_get_mode(sre_plan_t p, sre_mode_t *mode) {
+    if (!p || !mode) return SRE_EINVAL;
+    *mode = p->mode;
+    return SRE_OK;
+}
+
+sre_status_t sre_plan_set_profiling(sre_plan_t p, int enable) {
+    if (!p) return SRE_EINVAL;
+    p->profiling = enable != 0;
+    if (p->profiling && !p->ws.ev_begin) {
+        cudaError_t e = cudaEventCreate(&p->ws.ev_begin);
+        if (e == cudaSuccess) e = cudaEventCreate(&p->ws.ev_end);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (!p->profiling && p->ws.ev_begin) {
+        cudaStreamSynchronize(0);
+        cudaEventDestroy(p->ws.ev_begin);
+        cudaEventDestroy(p->ws.ev_end);
+        p->ws.ev_begin = p->ws.ev_end = nullptr;
+    }
+    return SRE_OK;
+}
+
+sre_status_t sre_plan_last_kernel_ms(sre_plan_t p, double *ms, const char **name) {
+    if (!p || !ms) return SRE_EINVAL;
+    if (!p->ws.ev_begin) return SRE_EINVAL;
+    cudaError_t e = cudaEventSynchronize(p->ws.ev_end);
+    if (e != cudaSuccess) return cuda_fail(e);
+    float f = 0.f;
+    e = cudaEventElapsedTime(&f, p->ws.ev_begin, p->ws.ev_end);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *ms = f;
+    if (name) *name = p->ws.main_kernel;
+    return SRE_OK;
+}
+
+sre_status_t sre_plan_launch_count(sre_plan_t p, uint64_t *count) {
+    if (!p || !count) return SRE_EINVAL;
+    *count = p->ws.launches + p->extra_launches;
+    return SRE_OK;
+}
+
+sre_status_t sre_plan_destroy(sre_plan_t p) {
+    if (!p) return SRE_OK;
+    cudaDeviceSynchronize();
+    sre::batched_destroy(p->batched);
+    sre::workspace_free(&p->ws);
+    cudaFreeHost(p->h_result);
+    cudaFree(p->d_stage);
+    delete p;
+    return SRE_OK;
+}
+
+static sre_status_t enqueue_plan(sre_plan_t p, const void *d_state, int N, uint64_t xb, uint64_t xe,
+                                 cudaStream_t st, double *d_m2, double *d_per_x) {
+    cudaError_t e;
+    if (sre::tc_mode_available(p->mode) && p->mode != SRE_MODE_FP32 && p->mode != SRE_MODE_FP64)
+        e = sre::tc_enqueue_m2(p->ws, p->dev, d_state, p->dtype, N, xb, xe, p->mode, st, d_m2,
+                               d_per_x, p->wait_ns);
+    else
+        e = sre::enqueue_m2(p->ws, p->dev, d_state, p->dtype, N, xb, xe, p->mode, st, d_m2,
+                            d_per_x, p->wait_ns, nullptr);
+    return e == cudaSuccess ? SRE_OK : cuda_fail(e);
+}
+
+static sre_status_t read_result(sre_plan_t p, cudaStream_t st, double *m2_host) {
+    cudaError_t e = cudaMemcpyAsync(p->h_result, p->ws.result, sizeof(sre::Result),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (p->h_result->status != 0) return (sre_status_t)p->h_result->status;
+    *m2_host = p->h_result->m2;
+    return SRE_OK;
+}
+
+sre_status_t sre_m2(sre_plan_t p, const void *d_state, int N, sre_stream_t stream, double *m2_host) {
+    sre_status_t s = check_state(p, d_state, N);
+    if (s != SRE_OK) return s;
+    if (!m2_host) return SRE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    s = enqueue_plan(p, d_state, N, 0, 1ull << N, st, nullptr, nullptr);
+    if (s != SRE_OK) return s;
+    return read_result(p, st, m2_host);
+}
+
+sre_status_t sre_m2_async(sre_plan_t p, const void *d_state, int N, sre_stream_t stream, double *d_m2) {
+    sre_status_t s = check_state(p, d_state, N);
+    if (s != SRE_OK) return s;
+    if (!d_m2) return SRE_EINVAL;
+    if (((uintptr_t)d_m2) % 8) return SRE_EALIGN;
+    return enqueue_plan(p, d_state, N, 0, 1ull << N, (cudaStream_t)stream, d_m2, nullptr);
+}
+
+sre_status_t sre_m2_host(sre_plan_t p, const void *h_state, int N, sre_stream_t stream,
+                         double *m2_host) {
+    if (!p || !h_state || !m2_host) return SRE_EINVAL;
+    if (N < 1 || N > p->N) return SRE_EINVAL;
+    const size_t bytes = (size_t)dtype_bytes(p->dtype) << N;
+    if (!p->d_stage || p->d_stage_bytes < bytes) {
+        cudaFree(p->d_stage);
+        p->d_stage = nullptr;
+        p->d_stage_bytes = 0;
+        const size_t cap = (size_t)dtype_bytes(p->dtype) << p->N;
+        cudaError_t e = cudaMalloc(&p->d_stage, cap);
+        if (e != cudaSuccess) return cuda_fail(e);
+        p->d_stage_bytes = cap;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(p->d_stage, h_state, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    sre_status_t s = enqueue_plan(p, p->d_stage, N, 0, 1ull << N, st, nullptr, nullptr);
+    if (s != SRE_OK) return s;
+    return read_result(p, st, m2_host);
+}
+
+sre_status_t sre_sum4_range(sre_plan_t p, const void *d_state, int N, uint64_t x_begin,
+                            uint64_t x_end, sre_stream_t stream, double *d_out, double *d_per_x) {
+    sre_status_t s = check_state(p, d_state, N);
+    if (s != SRE_OK) return s;
+    if (!d_out || x_begin >= x_end || x_end > (1ull << N)) return SRE_EINVAL;
+    if (d_per_x && N <= sre::kTileBits) return SRE_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    s = enqueue_plan(p, d_state, N, x_begin, x_end, st, nullptr, d_per_x);
+    if (s != SRE_OK) return s;
+    cudaError_t e = sre::enqueue_copy_sums(p->ws, d_out, st);
+    return e == cudaSuccess ? SRE_OK : cuda_fail(e);
+}
+
+sre_status_t sre_m2_batched(sre_plan_t p, const void *const *d_states, const int *Ns, int count,
+                            sre_stream_t stream, double *d_m2_out) {
+    if (!p || !d_states || !Ns || !d_m2_out || count < 1) return SRE_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        sre_status_t s = check_state(p, d_states[i], Ns[i]);
+        if (s != SRE_OK) return s;
+    }
+    if (!p->batched) {
+        p->batched = sre::batched_create(p->dev);
+        if (!p->batched) return SRE_ENOMEM;
+    }
+    cudaError_t e = sre::batched_run(p->batched, p->ws, p->dev, d_states, Ns, count, p->dtype,
+                                     p->mode, (cudaStream_t)stream, d_m2_out, p->wait_ns);
+    return e == cudaSuccess ? SRE_OK : cuda_fail(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// sre_internal.h -- host-side declarations shared by the libsre translation
+// units (kernels, plan / C ABI, batched path, server).  Not installed.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sre.h"
+
+namespace sre {
+
+constexpr int kTileBits = 12;              // one CTA tile: 2^12 complex entries
+constexpr int kTile = 1 << kTileBits;
+constexpr int kThreads = 256;              // threads per tile CTA
+constexpr int kPerThread = kTile / kThreads;  // 16 entries per thread (4 register bits)
+constexpr int kNormBlocks = 264;           // fixed grid of the norm reduction
+constexpr int kFinalThreads = 256;
+
+// Device-side result block of one evaluation (written by the finalize kernel).
+struct Result {
+    double m2;     // -log2(S / (d n2^4)), NaN on a zero / non-finite state
+    double S;      // sum_{x,z} |A_x(z)|^4 over the evaluated shift range
+    double n2;     // <psi|psi>
+    int status;    // sre_status_t of the data checks and device waits
+    int pad;
+};
+
+// Error word bits written by kernels.
+constexpr int kFlagNonFinite = 1;
+
+// Launch configuration of the two-pass (N > 12) persistent kernel.
+struct LargeCfg {
+    int C_log;   // log2 shifts per chunk (shared partner tile in pass 1)
+    int R;       // ring slots of inter-pass scratch
+    int G2_log;  // log2 tiles per pass-2 work item
+    int grid;    // persistent CTAs
+};
+
+// Everything one evaluation needs on the device (owned by a plan or a
+// batched / server context).
+struct Workspace {
+    int N_max = 0;
+    int elem_bytes = 8;            // 8 (FP32 complex) or 16 (FP64 complex)
+    double *npart = nullptr;       // kNormBlocks
+    int *flags = nullptr;          // 1 int: data flags (non-finite)
+    double *part = nullptr;        // per-CTA partials of the single-tile path
+    int part_cap = 0;
+    void *scratch = nullptr;       // ring of inter-pass scratch
+    size_t scratch_bytes = 0;
+    double *item_part = nullptr;   // ring of pass-2 item partials
+    size_t item_part_cap = 0;
+    double *chunk_sum = nullptr;   // per-chunk sums
+    size_t chunk_cap = 0;
+    unsigned *counters = nullptr;  // done1 | done2 | freed, chunk_cap each
+    unsigned long long *work = nullptr;  // work-queue counter
+    int *status = nullptr;         // device status word
+    Result *result = nullptr;      // device result block
+    void *conv = nullptr;          // state converted to the compute type (lazy)
+    size_t conv_bytes = 0;
+    // profiling: events recorded around the main transform kernel when set
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+    mutable const char *main_kernel = "";
+    mutable unsigned long long launches = 0;  // kernels launched through this workspace
+};
+
+struct DeviceInfo {
+    int device = 0;
+    int sms = 0;
+    int l2_bytes = 0;
+    int max_smem_optin = 0;
+};
+
+cudaError_t query_device(DeviceInfo *info);
+
+// Pick the two-pass configuration for N > 12.
+LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, sre_mode_t mode);
+
+// Bytes of workspace needed for states up to N_max with element size.
+size_t workspace_scratch_bytes(const DeviceInfo &dev, int N_max, int elem_bytes, sre_mode_t mode);
+
+cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int elem_bytes,
+                            sre_mode_t mode);
+void workspace_free(Workspace *ws);
+
+// Enqueue the sum over shifts [x_begin, x_end) and the norm of one state.
+// The result block (m2, S, n2, status) lands in ws->result; if d_m2 is not
+// null M2 is also written there; if d_per_x is not null and N > 12 each
+// shift's sum is written there.  mode: SRE_MODE_FP32 or SRE_MODE_FP64.
+cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d_state,
+                       sre_dtype_t dtype, int N, uint64_t x_begin, uint64_t x_end,
+                       sre_mode_t mode, cudaStream_t stream, double *d_m2, double *d_per_x,
+                       long long wait_ns, LargeCfg *cfg_override);
+
+// Copy the result block to d_out2 = {S, n2} (for the range API).
+cudaError_t enqueue_copy_sums(const Workspace &ws, double *d_out2, cudaStream_t stream);
+
+}  // namespace sre

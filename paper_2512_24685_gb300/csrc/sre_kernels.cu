@@ -1,0 +1,595 @@
+// sre_kernels.cu -- CUDA-core XOR-FWHT path of libsre (FP32 and FP64).
+//
+// Algorithm 1 of the paper: for every shift x, form the XOR-shifted product
+// g_x(t) = conj(phi_{t^x}) phi_t, transform it with the unnormalised FWHT over
+// t (A_x(z) = <psi|X^x Z^z|psi>, Eq. (Pauli_expect)) and accumulate
+// sum_z |A_x(z)|^4; M2 = -log2(S / (d n2^4)) (Eq. (final1), base 2).
+//
+// Kernels
+//   k_convert   element-type conversion of the state (complex128 <-> complex64)
+//   k_norm      n2 = <psi|psi> in FP64 + NaN/Inf detection (fixed grid)
+//   k_small     N <= 12: one 2^12-entry tile holds 2^(12-N) whole shifts; the
+//               state sits in shared memory; static tile->CTA assignment
+//   k_large     N  > 12: persistent two-pass kernel.  Pass 1 (one work item
+//               per chunk of C shifts and high index block t_h) forms the
+//               products of a 2^12 block, transforms its 12 low bits and
+//               writes the block to an L2-sized ring of scratch; pass 2 (work
+//               items of whole-z-block tiles) gathers the 2^(N-12) blocks of
+//               a z-range, transforms the high bits and reduces |A|^4.  Items
+//               are claimed in order from one counter; pass 2 of a chunk waits
+//               (bounded, %globaltimer) for its pass-1 items, and pass 1 of a
+//               chunk waits for the ring slot to be released.
+//   k_finalize  fixed-order FP64 sums of the partials, M2 and the status.
+// Every reduction has a fixed order, so results are bitwise reproducible and
+// do not depend on what else runs on the device.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "sre_internal.h"
+#include "sre_tile.cuh"
+
+namespace sre {
+using namespace dev;
+
+// ---------------------------------------------------------------- helpers
+
+template <typename Out, typename In>
+__global__ void k_convert(const In *__restrict__ src, Out *__restrict__ dst, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const In v = src[i];
+        Out o;
+        o.x = (decltype(o.x))v.x;
+        o.y = (decltype(o.y))v.y;
+        dst[i] = o;
+    }
+}
+
+// n2 = sum_t |phi_t|^2 (FP64), per-block partials in a fixed grid.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_norm(const v2_t<R> *__restrict__ psi, uint64_t d,
+                                                   double *__restrict__ npart,
+                                                   int *__restrict__ flags) {
+    __shared__ double red[kThreads / 32];
+    double s = 0.0;
+    int bad = 0;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < d;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const v2_t<R> v = psi[t];
+        const double re = (double)v.x, im = (double)v.y;
+        if (!isfinite(re) || !isfinite(im)) bad = 1;
+        s += re * re + im * im;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagNonFinite);
+    const double b = block_sum(s, red);
+    if (threadIdx.x == 0) npart[blockIdx.x] = b;
+}
+
+// ------------------------------------------------------- N <= 12: k_small
+
+// Tile g covers flat indices [g*4096, (g+1)*4096) of the (x - x_begin, t)
+// space: x = x_begin + (flat >> N), t = flat & (d - 1).  The transform runs
+// over the low NB = N bits of the tile index.
+template <typename R, int NB>
+__global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ psi,
+                                                    uint64_t x_begin, uint64_t x_end,
+                                                    long long ntiles,
+                                                    double *__restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using V = v2_t<R>;
+    V *psi_s = reinterpret_cast<V *>(smem_raw);
+    V *bufA = psi_s + kTile;
+    V *bufB = bufA + kTile;
+    __shared__ double red[kThreads / 32];
+    constexpr int N = NB;
+    constexpr int d = 1 << N;
+    const int tid = threadIdx.x;
+    for (int t = tid; t < d; t += kThreads) psi_s[swz(t)] = psi[t];
+    __syncthreads();
+
+    double acc = 0.0;
+    for (long long g = blockIdx.x; g < ntiles; g += gridDim.x) {
+        R re[16], im[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const uint64_t flat = ((uint64_t)g << kTileBits) | (uint64_t)elem<0>(tid, i);
+            const uint64_t x = x_begin + (flat >> N);
+            const int t = (int)(flat & (d - 1));
+            if (x < x_end) {
+                const V a = psi_s[swz(t)];
+                const V b = psi_s[swz(t ^ (int)x)];
+                // conj(phi_{t^x}) * phi_t
+                re[i] = b.x * a.x + b.y * a.y;
+                im[i] = b.x * a.y - b.y * a.x;
+            } else {
+                re[i] = R(0);
+                im[i] = R(0);
+            }
+        }
+        tile_fwht<NB>(re, im, bufA, bufB, tid);
+        acc += (double)sum_abs4(re, im);
+        __syncthreads();
+    }
+    const double s = block_sum(acc, red);
+    if (tid == 0) part[blockIdx.x] = s;
+}
+
+// -------------------------------------------------------- N > 12: k_large
+
+struct LargeArgs {
+    const void *psi;
+    int N, h;                  // h = N - 12 high bits done in pass 2
+    uint64_t x_begin, x_end;   // evaluated shift range
+    uint64_t x0;               // x_begin rounded down to a chunk boundary
+    int C_log, R, G2_log;
+    long long n_chunks;
+    int P1, P2;                // items per chunk in pass 1 / pass 2
+    long long n_items;
+    void *scratch;             // R * C * 2^N complex
+    double *item_part;         // R * P2
+    double *chunk_sum;         // n_chunks
+    unsigned *done1, *done2, *freed;  // n_chunks each
+    unsigned long long *work;
+    double *per_x;             // optional, indexed by x - x_begin
+    int *status;
+    long long wait_ns;
+};
+
+// Thread 0 waits until *p >= target.  Bounded by wait_ns of %globaltimer and
+// by an iteration cap; on expiry it records SRE_ETIMEDOUT and returns false.
+// Returns false as well if another CTA already recorded an error.
+__device__ bool wait_counter(const unsigned *p, unsigned target, int *status, long long wait_ns) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned it = 0; it < (1u << 30); ++it) {
+        if (ld_acquire_u32(p) >= target) return true;
+        if (*(volatile int *)status != 0) return false;
+        if ((it & 31) == 31 && (long long)(globaltimer_ns() - t0) > wait_ns) break;
+        __nanosleep(64);
+    }
+    atomicCAS(status, 0, (int)SRE_ETIMEDOUT);
+    return false;
+}
+
+template <typename R, int H>
+__global__ void __launch_bounds__(kThreads) k_large(LargeArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using V = v2_t<R>;
+    V *tileS = reinterpret_cast<V *>(smem_raw);  // partner tile (pass 1) / staging (pass 2)
+    V *bufA = tileS + kTile;
+    V *bufB = bufA + kTile;
+    __shared__ double red[kThreads / 32];
+    __shared__ long long s_item;
+    __shared__ int s_flag;
+
+    const int tid = threadIdx.x;
+    const int N = a.N;
+    const uint64_t d = 1ull << N;
+    const int C = 1 << a.C_log;
+    const V *psi = reinterpret_cast<const V *>(a.psi);
+    V *scratch = reinterpret_cast<V *>(a.scratch);
+    constexpr int zsub_bits = kTileBits - H;  // z entries per block in pass 2
+    const int ipx_log = H - a.G2_log;         // pass-2 items per shift (log2)
+
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(a.work, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= a.n_items) break;
+        const long long c = item / (a.P1 + a.P2);
+        const int r = (int)(item - c * (a.P1 + a.P2));
+        const int slot = (int)(c % a.R);
+        const uint64_t xc = a.x0 + ((uint64_t)c << a.C_log);
+        V *slot_base = scratch + (size_t)slot * ((size_t)C << N);
+
+        if (r < a.P1) {
+            // ---------------- pass 1: block t_h = r of every shift in the chunk
+            const int th = r;
+            if (tid == 0) {
+                s_flag = 1;
+                if (c >= a.R) s_flag = wait_counter(a.freed + (c - a.R), 1u, a.status, a.wait_ns);
+            }
+            __syncthreads();
+            if (!s_flag) break;
+            const uint64_t xh = xc >> kTileBits;
+            const int xl0 = (int)(xc & (kTile - 1));
+            const V *pb = psi + (((uint64_t)th ^ xh) << kTileBits);
+            for (int j = tid; j < kTile; j += kThreads) tileS[swz(j)] = pb[j];
+            R ar[16], ai[16];
+            const V *pa = psi + ((uint64_t)th << kTileBits) + (tid << 4);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const V v = pa[i];
+                ar[i] = v.x;
+                ai[i] = v.y;
+            }
+            __syncthreads();
+            for (int xl = 0; xl < C; ++xl) {
+                const uint64_t x = xc + (uint64_t)xl;
+                if (x < a.x_begin || x >= a.x_end) continue;
+                const int xlow = xl0 + xl;
+                R re[16], im[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const V b = tileS[swz(elem<0>(tid, i) ^ xlow)];
+                    re[i] = b.x * ar[i] + b.y * ai[i];
+                    im[i] = b.x * ai[i] - b.y * ar[i];
+                }
+                tile_fwht<kTileBits>(re, im, bufA, bufB, tid);
+                V *o = slot_base + ((size_t)xl << N) + ((size_t)th << kTileBits);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    V v;
+                    v.x = re[i];
+                    v.y = im[i];
+                    __stcg(o + elem<2>(tid, i), v);
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(a.done1 + c, 1u);
+            }
+        } else {
+            // ---------------- pass 2: 2^G2 z-blocks of one shift
+            const int j = r - a.P1;
+            const int xl = j >> ipx_log;
+            const int zb0 = (j & ((1 << ipx_log) - 1)) << a.G2_log;
+            if (tid == 0) s_flag = wait_counter(a.done1 + c, (unsigned)a.P1, a.status, a.wait_ns);
+            __syncthreads();
+            if (!s_flag) break;
+            __threadfence();
+            const uint64_t x = xc + (uint64_t)xl;
+            double acc = 0.0;
+            if (x >= a.x_begin && x < a.x_end) {
+                const V *xb = slot_base + ((size_t)xl << N);
+                for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
+                    const int zb = zb0 + gb;
+                    __syncthreads();
+                    for (int q = tid; q < kTile; q += kThreads) {
+                        const int zs = q & ((1 << zsub_bits) - 1);
+                        const int th = q >> zsub_bits;
+                        const V v = __ldcg(xb + ((size_t)th << kTileBits) + (zb << zsub_bits) + zs);
+                        tileS[swz((zs << H) | th)] = v;
+                    }
+                    __syncthreads();
+                    R re[16], im[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const V v = tileS[swz(elem<0>(tid, i))];
+                        re[i] = v.x;
+                        im[i] = v.y;
+                    }
+                    tile_fwht<H>(re, im, bufA, bufB, tid);
+                    acc += (double)sum_abs4(re, im);
+                }
+            }
+            const double s = block_sum(acc, red);
+            if (tid == 0) {
+                a.item_part[(size_t)slot * a.P2 + j] = s;
+                __threadfence();
+                const unsigned old = atomicAdd(a.done2 + c, 1u);
+                s_flag = (old == (unsigned)a.P2 - 1u);
+            }
+            __syncthreads();
+            if (s_flag) {
+                // last pass-2 item of the chunk: per-shift and chunk sums in fixed order
+                __threadfence();
+                double ps = 0.0;
+                for (int q = tid; q < C; q += kThreads) {
+                    double sx = 0.0;
+                    const double *ip = a.item_part + (size_t)slot * a.P2 + ((size_t)q << ipx_log);
+                    for (int k = 0; k < (1 << ipx_log); ++k) sx += __ldcg(ip + k);
+                    const uint64_t xq = xc + (uint64_t)q;
+                    if (a.per_x && xq >= a.x_begin && xq < a.x_end) a.per_x[xq - a.x_begin] = sx;
+                    ps += sx;
+                }
+                const double cs = block_sum(ps, red);
+                if (tid == 0) {
+                    a.chunk_sum[c] = cs;
+                    __threadfence();
+                    atomicExch(a.freed + c, 1u);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------- finalize
+
+__global__ void __launch_bounds__(kFinalThreads) k_finalize(const double *__restrict__ parts,
+                                                            long long nparts,
+                                                            const double *__restrict__ npart,
+                                                            int nn, int N, const int *flags,
+                                                            const int *status, Result *res,
+                                                            double *d_m2) {
+    __shared__ double red[kFinalThreads / 32];
+    double s = 0.0;
+    for (long long k = threadIdx.x; k < nparts; k += blockDim.x) s += parts[k];
+    const double S = block_sum(s, red);
+    double n = 0.0;
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) n += npart[k];
+    const double n2 = block_sum(n, red);
+    if (threadIdx.x == 0) {
+        int st = *status;
+        if (st == 0 && (*flags & kFlagNonFinite)) st = SRE_ENONFINITE;
+        if (st == 0 && !(n2 > 0.0)) st = SRE_EZERO;
+        // M2 = -log2(S / (d n2^4)), written in logs so tiny norms do not underflow
+        const double m2 = st ? __longlong_as_double(0x7ff8000000000000ll)
+                             : -(log2(S) - (double)N - 4.0 * log2(n2));
+        res->m2 = m2;
+        res->S = S;
+        res->n2 = n2;
+        res->status = st;
+        if (d_m2) *d_m2 = m2;
+    }
+}
+
+__global__ void k_copy_sums(const Result *res, double *out2) {
+    out2[0] = res->S;
+    out2[1] = res->n2;
+}
+
+// ------------------------------------------------------------ host side
+
+cudaError_t query_device(DeviceInfo *info) {
+    cudaError_t e = cudaGetDevice(&info->device);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&info->sms, cudaDevAttrMultiProcessorCount, info->device);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&info->l2_bytes, cudaDevAttrL2CacheSize, info->device);
+    if (e != cudaSuccess) return e;
+    return cudaDeviceGetAttribute(&info->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                  info->device);
+}
+
+static size_t tile_smem_bytes(int elem_bytes) { return (size_t)3 * kTile * elem_bytes; }
+
+LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, sre_mode_t mode) {
+    (void)mode;
+    LargeCfg c;
+    const int h = N - kTileBits;
+    const double per_x = (double)elem_bytes * (double)(1ull << N);
+    // ring of R slots of C shifts each, sized to stay within ~3/8 of L2
+    const double budget = std::max(16.0 * (1 << 20), 0.375 * (double)dev.l2_bytes);
+    c.R = 3;
+    int C_log = 0;
+    while (C_log < kTileBits && per_x * (double)(2 << C_log) * c.R <= budget) ++C_log;
+    c.C_log = C_log;
+    c.G2_log = std::min(C_log, h);
+    const int occ = elem_bytes == 8 ? 2 : 1;
+    c.grid = std::max(1, dev.sms * occ);
+    return c;
+}
+
+size_t workspace_scratch_bytes(const DeviceInfo &dev, int N_max, int elem_bytes, sre_mode_t mode) {
+    if (N_max <= kTileBits) return 0;
+    const LargeCfg c = choose_large_cfg(dev, N_max, elem_bytes, mode);
+    return (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)elem_bytes << N_max);
+}
+
+void workspace_free(Workspace *ws) {
+    if (ws->ev_begin) cudaEventDestroy(ws->ev_begin);
+    if (ws->ev_end) cudaEventDestroy(ws->ev_end);
+    cudaFree(ws->npart);
+    cudaFree(ws->flags);
+    cudaFree(ws->part);
+    cudaFree(ws->scratch);
+    cudaFree(ws->item_part);
+    cudaFree(ws->chunk_sum);
+    cudaFree(ws->counters);
+    cudaFree(ws->work);
+    cudaFree(ws->status);
+    cudaFree(ws->result);
+    cudaFree(ws->conv);
+    *ws = Workspace();
+}
+
+cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int elem_bytes,
+                            sre_mode_t mode) {
+    *ws = Workspace();
+    ws->N_max = N_max;
+    ws->elem_bytes = elem_bytes;
+    cudaError_t e;
+#define SRE_TRY(x)                  \
+    do {                            \
+        e = (x);                    \
+        if (e != cudaSuccess) {     \
+            workspace_free(ws);     \
+            return e;               \
+        }                           \
+    } while (0)
+    SRE_TRY(cudaMalloc(&ws->npart, sizeof(double) * kNormBlocks));
+    SRE_TRY(cudaMalloc(&ws->flags, sizeof(int)));
+    ws->part_cap = std::max(1, dev.sms * 4);
+    SRE_TRY(cudaMalloc(&ws->part, sizeof(double) * ws->part_cap));
+    SRE_TRY(cudaMalloc(&ws->work, sizeof(unsigned long long)));
+    SRE_TRY(cudaMalloc(&ws->status, sizeof(int)));
+    SRE_TRY(cudaMalloc(&ws->result, sizeof(Result)));
+    if (N_max > kTileBits) {
+        // sizes for the largest N; smaller N reuse the same buffers
+        size_t scratch = 0, item_cap = 0, chunk_cap = 0;
+        for (int n = kTileBits + 1; n <= N_max; ++n) {
+            const LargeCfg c = choose_large_cfg(dev, n, elem_bytes, mode);
+            const int h = n - kTileBits;
+            scratch = std::max(scratch, (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)elem_bytes << n));
+            const size_t P2 = ((size_t)1 << c.C_log) << (h - c.G2_log);
+            item_cap = std::max(item_cap, (size_t)c.R * P2);
+            chunk_cap = std::max(chunk_cap, ((size_t)1 << n) >> c.C_log);
+        }
+        ws->scratch_bytes = scratch;
+        ws->item_part_cap = item_cap;
+        ws->chunk_cap = chunk_cap;
+        SRE_TRY(cudaMalloc(&ws->scratch, scratch));
+        SRE_TRY(cudaMalloc(&ws->item_part, sizeof(double) * item_cap));
+        SRE_TRY(cudaMalloc(&ws->chunk_sum, sizeof(double) * chunk_cap));
+        SRE_TRY(cudaMalloc(&ws->counters, sizeof(unsigned) * 3 * chunk_cap));
+    }
+#undef SRE_TRY
+    return cudaSuccess;
+}
+
+template <typename R, int NB>
+static cudaError_t launch_small_nb(const void *psi, uint64_t x_begin, uint64_t x_end,
+                                   const Workspace &ws, const DeviceInfo &dev, cudaStream_t st,
+                                   int *nparts) {
+    const size_t smem = tile_smem_bytes(sizeof(v2_t<R>));
+    auto kern = k_small<R, NB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t flat = (x_end - x_begin) << NB;
+    const long long ntiles = (long long)((flat + kTile - 1) >> kTileBits);
+    const int occ = sizeof(R) == 4 ? 2 : 1;
+    const int grid = (int)std::min<long long>(ntiles, std::min(ws.part_cap, dev.sms * occ));
+    kern<<<grid, kThreads, smem, st>>>(reinterpret_cast<const v2_t<R> *>(psi), x_begin, x_end,
+                                       ntiles, ws.part);
+    *nparts = grid;
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_small(int N, const void *psi, uint64_t xb, uint64_t xe,
+                                const Workspace &ws, const DeviceInfo &dev, cudaStream_t st,
+                                int *nparts) {
+    switch (N) {
+#define SRE_CASE(n) \
+    case n: return launch_small_nb<R, n>(psi, xb, xe, ws, dev, st, nparts);
+        SRE_CASE(1) SRE_CASE(2) SRE_CASE(3) SRE_CASE(4) SRE_CASE(5) SRE_CASE(6)
+        SRE_CASE(7) SRE_CASE(8) SRE_CASE(9) SRE_CASE(10) SRE_CASE(11) SRE_CASE(12)
+#undef SRE_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R, int H>
+static cudaError_t launch_large_h(const LargeArgs &a, int grid, cudaStream_t st) {
+    const size_t smem = tile_smem_bytes(sizeof(v2_t<R>));
+    auto kern = k_large<R, H>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_large(const LargeArgs &a, int grid, cudaStream_t st) {
+    switch (a.h) {
+#define SRE_CASE(n) \
+    case n: return launch_large_h<R, n>(a, grid, st);
+        SRE_CASE(1) SRE_CASE(2) SRE_CASE(3) SRE_CASE(4) SRE_CASE(5) SRE_CASE(6)
+        SRE_CASE(7) SRE_CASE(8) SRE_CASE(9) SRE_CASE(10) SRE_CASE(11) SRE_CASE(12)
+#undef SRE_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t enqueue_copy_sums(const Workspace &ws, double *d_out2, cudaStream_t stream) {
+    k_copy_sums<<<1, 1, 0, stream>>>(ws.result, d_out2);
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, const void *psi, int N,
+                                uint64_t x_begin, uint64_t x_end, cudaStream_t st, double *d_m2,
+                                double *d_per_x, long long wait_ns, LargeCfg *cfg_override) {
+    cudaError_t e;
+    const uint64_t d = 1ull << N;
+    if ((e = cudaMemsetAsync(ws.flags, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws.status, 0, sizeof(int), st)) != cudaSuccess) return e;
+    k_norm<R><<<kNormBlocks, kThreads, 0, st>>>(reinterpret_cast<const v2_t<R> *>(psi), d, ws.npart,
+                                                ws.flags);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ws.launches += 2;  // k_norm + k_finalize
+    const double *parts = nullptr;
+    long long nparts = 0;
+    if (N <= kTileBits) {
+        int np = 0;
+        if (ws.ev_begin && (e = cudaEventRecord(ws.ev_begin, st)) != cudaSuccess) return e;
+        if ((e = launch_small<R>(N, psi, x_begin, x_end, ws, dev, st, &np)) != cudaSuccess) return e;
+        if (ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
+        ws.main_kernel = "k_small";
+        ws.launches += 1;
+        parts = ws.part;
+        nparts = np;
+    } else {
+        LargeCfg c = cfg_override ? *cfg_override : choose_large_cfg(dev, N, sizeof(v2_t<R>),
+                                                                     SRE_MODE_FP32);
+        LargeArgs a;
+        a.psi = psi;
+        a.N = N;
+        a.h = N - kTileBits;
+        a.x_begin = x_begin;
+        a.x_end = x_end;
+        a.C_log = c.C_log;
+        a.R = c.R;
+        a.G2_log = std::min(c.G2_log, a.h);
+        a.x0 = x_begin & ~((1ull << c.C_log) - 1);
+        a.n_chunks = (long long)((x_end - a.x0 + (1ull << c.C_log) - 1) >> c.C_log);
+        a.P1 = 1 << a.h;
+        a.P2 = (1 << c.C_log) << (a.h - a.G2_log);
+        a.n_items = a.n_chunks * (long long)(a.P1 + a.P2);
+        const size_t need_scratch = (size_t)c.R * ((size_t)1 << c.C_log) * (sizeof(v2_t<R>) << N);
+        if (need_scratch > ws.scratch_bytes || (size_t)a.n_chunks > ws.chunk_cap ||
+            (size_t)c.R * a.P2 > ws.item_part_cap)
+            return cudaErrorInvalidValue;
+        a.scratch = ws.scratch;
+        a.item_part = ws.item_part;
+        a.chunk_sum = ws.chunk_sum;
+        a.done1 = ws.counters;
+        a.done2 = ws.counters + ws.chunk_cap;
+        a.freed = ws.counters + 2 * ws.chunk_cap;
+        a.work = ws.work;
+        a.per_x = d_per_x;
+        a.status = ws.status;
+        a.wait_ns = wait_ns;
+        if ((e = cudaMemsetAsync(ws.counters, 0, sizeof(unsigned) * 3 * ws.chunk_cap, st)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(ws.work, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        const int grid = (int)std::max<long long>(1, std::min<long long>(c.grid, a.n_items));
+        if (ws.ev_begin && (e = cudaEventRecord(ws.ev_begin, st)) != cudaSuccess) return e;
+        if ((e = launch_large<R>(a, grid, st)) != cudaSuccess) return e;
+        if (ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
+        ws.main_kernel = "k_large";
+        ws.launches += 1;
+        parts = ws.chunk_sum;
+        nparts = a.n_chunks;
+    }
+    k_finalize<<<1, kFinalThreads, 0, st>>>(parts, nparts, ws.npart, kNormBlocks, N, ws.flags,
+                                            ws.status, ws.result, d_m2);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d_state,
+                       sre_dtype_t dtype, int N, uint64_t x_begin, uint64_t x_end,
+                       sre_mode_t mode, cudaStream_t stream, double *d_m2, double *d_per_x,
+                       long long wait_ns, LargeCfg *cfg_override) {
+    const bool fp64 = (mode == SRE_MODE_FP64);
+    const int want = fp64 ? SRE_C128 : SRE_C64;
+    const void *psi = d_state;
+    const uint64_t d = 1ull << N;
+    if ((int)dtype != want) {
+        const size_t need = (size_t)d * (fp64 ? 16 : 8);
+        if (!ws.conv || ws.conv_bytes < need) return cudaErrorInvalidValue;
+        const int grid = (int)std::min<uint64_t>((d + kThreads - 1) / kThreads, 4096);
+        if (fp64)
+            k_convert<double2, float2><<<grid, kThreads, 0, stream>>>(
+                reinterpret_cast<const float2 *>(d_state), reinterpret_cast<double2 *>(ws.conv), d);
+        else
+            k_convert<float2, double2><<<grid, kThreads, 0, stream>>>(
+                reinterpret_cast<const double2 *>(d_state), reinterpret_cast<float2 *>(ws.conv), d);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        ws.launches += 1;
+        psi = ws.conv;
+    }
+    if (fp64)
+        return enqueue_m2_t<double>(ws, dev, psi, N, x_begin, x_end, stream, d_m2, d_per_x, wait_ns,
+                                    cfg_override);
+    return enqueue_m2_t<float>(ws, dev, psi, N, x_begin, x_end, stream, d_m2, d_per_x, wait_ns,
+                               cfg_override);
+}
+
+}  // namespace sre

@@ -31,6 +31,7 @@ constexpr int kFlagNonFinite = 1;
 struct LargeCfg {
     int C_log;   // log2 shifts per chunk (shared partner tile in pass 1)
     int R;       // ring slots of inter-pass scratch
+    int D;       // lag (in chunks) of pass 2 behind pass 1, D < R
     int G2_log;  // log2 tiles per pass-2 work item
     int grid;    // persistent CTAs
 };
@@ -51,7 +52,7 @@ struct Workspace {
     double *chunk_sum = nullptr;   // per-chunk sums
     size_t chunk_cap = 0;
     unsigned *counters = nullptr;  // done1 | done2 | freed, chunk_cap each
-    unsigned long long *work = nullptr;  // work-queue counter
+    unsigned long long *work = nullptr;  // work-queue counters (full, halved)
     int *status = nullptr;         // device status word
     Result *result = nullptr;      // device result block
     void *conv = nullptr;          // state converted to the compute type (lazy)
@@ -71,8 +72,9 @@ struct DeviceInfo {
 
 cudaError_t query_device(DeviceInfo *info);
 
-// Pick the two-pass configuration for N > 12.
-LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, sre_mode_t mode);
+// Pick the two-pass configuration for N > 12 (half: conjugate-symmetry halved
+// shifts, x >= 4096).
+LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half);
 
 // Bytes of workspace needed for states up to N_max with element size.
 size_t workspace_scratch_bytes(const DeviceInfo &dev, int N_max, int elem_bytes, sre_mode_t mode);

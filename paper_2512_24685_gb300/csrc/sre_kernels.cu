@@ -119,16 +119,40 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
 
 // -------------------------------------------------------- N > 12: k_large
 
+// Work of one evaluation over shifts [x_begin, x_end), N > 12.
+//
+// Shifts are grouped in chunks of C = 2^C_log consecutive values (aligned, so
+// a chunk shares x_h = x >> 12 and, for halved chunks, the pivot bit).  A
+// chunk owns one slot of a ring of R scratch slots.  Its work items:
+//   pass 1, P1 = 2^h2 items: block t'_h of every shift of the chunk -- the
+//           XOR-shifted products of one 2^12 block of t, the 12 low transform
+//           bits, written to scratch[slot][shift][t'_h][z_l];
+//   pass 2, P2 items of 2^G2_log tiles: for one shift and a range of z-blocks,
+//           the 2^h2 blocks t'_h of each z-block are read back, the h2 high
+//           bits are transformed and |A|^4 is reduced.
+// Items are claimed from one counter in a lagged order -- step s holds the
+// pass-1 items of chunk s and the pass-2 items of chunk s - D -- so pass 2
+// rarely waits for pass 1; pass 1 of chunk c waits for slot c % R to be
+// released by chunk c - R (D < R keeps this deadlock-free: every item waits
+// only on items claimed before it).
+//
+// Halving (half = 1, shifts x >= 4096).  With pivot j = the highest set bit
+// of x, g_x(t ^ x) = conj(g_x(t)) pairs every t with t_j = 1 to one with
+// t_j = 0, and sum_z |A_x(z)|^4 = 16 sum_{z'} [(Re W(z'))^4 + (Im W(z'))^4]
+// where W is the (N-1)-bit transform of g_x restricted to t_j = 0.  Since
+// j >= 12, the restriction removes one high bit: block t'_h maps to
+// t_h = t'_h with a zero inserted at bit j - 12, and h2 = N - 13.
 struct LargeArgs {
     const void *psi;
-    int N, h;                  // h = N - 12 high bits done in pass 2
+    int N, h2;                 // h2: pass-2 transform bits (N - 12, or N - 13 halved)
+    int half;
     uint64_t x_begin, x_end;   // evaluated shift range
     uint64_t x0;               // x_begin rounded down to a chunk boundary
-    int C_log, R, G2_log;
+    int C_log, R, D, G2_log;
     long long n_chunks;
     int P1, P2;                // items per chunk in pass 1 / pass 2
     long long n_items;
-    void *scratch;             // R * C * 2^N complex
+    void *scratch;             // R * C * 2^(N - half) complex
     double *item_part;         // R * P2
     double *chunk_sum;         // n_chunks
     unsigned *done1, *done2, *freed;  // n_chunks each
@@ -153,11 +177,44 @@ __device__ bool wait_counter(const unsigned *p, unsigned target, int *status, lo
     return false;
 }
 
-template <typename R, int H>
-__global__ void __launch_bounds__(kThreads) k_large(LargeArgs a) {
+// item -> (chunk, index within its pass, pass) for the lagged order.
+__device__ __forceinline__ void decode_item(const LargeArgs &a, long long item, long long &chunk,
+                                            int &r, bool &pass1) {
+    const long long D = a.D, P1 = a.P1, P2 = a.P2, n = a.n_chunks;
+    if (item < D * P1) {
+        chunk = item / P1;
+        r = (int)(item - chunk * P1);
+        pass1 = true;
+        return;
+    }
+    item -= D * P1;
+    const long long mid = (n - D) * (P1 + P2);
+    if (item < mid) {
+        const long long s = item / (P1 + P2);
+        const int q = (int)(item - s * (P1 + P2));
+        if (q < P1) {
+            chunk = D + s;
+            r = q;
+            pass1 = true;
+        } else {
+            chunk = s;
+            r = q - (int)P1;
+            pass1 = false;
+        }
+        return;
+    }
+    item -= mid;
+    const long long s = item / P2;
+    chunk = n - D + s;
+    r = (int)(item - s * P2);
+    pass1 = false;
+}
+
+template <typename R, int H2, bool HALF>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(LargeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = v2_t<R>;
-    V *tileS = reinterpret_cast<V *>(smem_raw);  // partner tile (pass 1) / staging (pass 2)
+    V *tileS = reinterpret_cast<V *>(smem_raw);  // partner block (pass 1)
     V *bufA = tileS + kTile;
     V *bufB = bufA + kTile;
     __shared__ double red[kThreads / 32];
@@ -165,28 +222,34 @@ __global__ void __launch_bounds__(kThreads) k_large(LargeArgs a) {
     __shared__ int s_flag;
 
     const int tid = threadIdx.x;
-    const int N = a.N;
-    const uint64_t d = 1ull << N;
+    const int lgx = a.N - (HALF ? 1 : 0);        // log2 scratch entries per shift
     const int C = 1 << a.C_log;
     const V *psi = reinterpret_cast<const V *>(a.psi);
     V *scratch = reinterpret_cast<V *>(a.scratch);
-    constexpr int zsub_bits = kTileBits - H;  // z entries per block in pass 2
-    const int ipx_log = H - a.G2_log;         // pass-2 items per shift (log2)
+    constexpr int zsub_bits = kTileBits - H2;     // z entries per block in pass 2
+    const int ipx_log = H2 - a.G2_log;            // pass-2 items per shift (log2)
 
     for (;;) {
         if (tid == 0) s_item = (long long)atomicAdd(a.work, 1ull);
         __syncthreads();
         const long long item = s_item;
         if (item >= a.n_items) break;
-        const long long c = item / (a.P1 + a.P2);
-        const int r = (int)(item - c * (a.P1 + a.P2));
+        long long c;
+        int r;
+        bool pass1;
+        decode_item(a, item, c, r, pass1);
         const int slot = (int)(c % a.R);
         const uint64_t xc = a.x0 + ((uint64_t)c << a.C_log);
-        V *slot_base = scratch + (size_t)slot * ((size_t)C << N);
+        V *slot_base = scratch + (size_t)slot * ((size_t)C << lgx);
 
-        if (r < a.P1) {
-            // ---------------- pass 1: block t_h = r of every shift in the chunk
-            const int th = r;
+        if (pass1) {
+            // ---------------- pass 1: block t'_h = r of every shift in the chunk
+            const int tp = r;
+            int th = tp;
+            if (HALF) {
+                const int jh = (63 - __clzll((long long)xc)) - kTileBits;
+                th = ((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1));
+            }
             if (tid == 0) {
                 s_flag = 1;
                 if (c >= a.R) s_flag = wait_counter(a.freed + (c - a.R), 1u, a.status, a.wait_ns);
@@ -214,11 +277,12 @@ __global__ void __launch_bounds__(kThreads) k_large(LargeArgs a) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const V b = tileS[swz(elem<0>(tid, i) ^ xlow)];
+                    // conj(phi_{t^x}) * phi_t
                     re[i] = b.x * ar[i] + b.y * ai[i];
                     im[i] = b.x * ai[i] - b.y * ar[i];
                 }
                 tile_fwht<kTileBits>(re, im, bufA, bufB, tid);
-                V *o = slot_base + ((size_t)xl << N) + ((size_t)th << kTileBits);
+                V *o = slot_base + ((size_t)xl << lgx) + ((size_t)tp << kTileBits);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     V v;
@@ -234,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) k_large(LargeArgs a) {
             }
         } else {
             // ---------------- pass 2: 2^G2 z-blocks of one shift
-            const int j = r - a.P1;
+            const int j = r;
             const int xl = j >> ipx_log;
             const int zb0 = (j & ((1 << ipx_log) - 1)) << a.G2_log;
             if (tid == 0) s_flag = wait_counter(a.done1 + c, (unsigned)a.P1, a.status, a.wait_ns);
@@ -244,26 +308,26 @@ __global__ void __launch_bounds__(kThreads) k_large(LargeArgs a) {
             const uint64_t x = xc + (uint64_t)xl;
             double acc = 0.0;
             if (x >= a.x_begin && x < a.x_end) {
-                const V *xb = slot_base + ((size_t)xl << N);
+                const V *xb = slot_base + ((size_t)xl << lgx);
                 for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
                     const int zb = zb0 + gb;
-                    __syncthreads();
-                    for (int q = tid; q < kTile; q += kThreads) {
-                        const int zs = q & ((1 << zsub_bits) - 1);
-                        const int th = q >> zsub_bits;
-                        const V v = __ldcg(xb + ((size_t)th << kTileBits) + (zb << zsub_bits) + zs);
-                        tileS[swz((zs << H) | th)] = v;
-                    }
-                    __syncthreads();
                     R re[16], im[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        const V v = tileS[swz(elem<0>(tid, i))];
+                        const int e = elem<0>(tid, i);
+                        const int tp = e & ((1 << H2) - 1);
+                        const int zs = e >> H2;
+                        const V v = __ldcg(xb + ((size_t)tp << kTileBits) + (zb << zsub_bits) + zs);
                         re[i] = v.x;
                         im[i] = v.y;
                     }
-                    tile_fwht<H>(re, im, bufA, bufB, tid);
-                    acc += (double)sum_abs4(re, im);
+                    // one relayout: alternate buffers between consecutive tiles
+                    V *b0 = (H2 > 4 && H2 <= 8 && (gb & 1)) ? bufB : bufA;
+                    tile_fwht<H2>(re, im, b0, bufB, tid);
+                    if (HALF)
+                        acc += 16.0 * (double)sum_re4_im4(re, im);
+                    else
+                        acc += (double)sum_abs4(re, im);
                 }
             }
             const double s = block_sum(acc, red);
@@ -348,27 +412,40 @@ cudaError_t query_device(DeviceInfo *info) {
 
 static size_t tile_smem_bytes(int elem_bytes) { return (size_t)3 * kTile * elem_bytes; }
 
-LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, sre_mode_t mode) {
-    (void)mode;
+// Ring / chunk configuration for the two-pass kernel.  The ring of R slots of
+// C shifts (scratch R * C * elem * 2^(N - half)) is kept within ~45% of L2 so
+// the inter-pass traffic stays on chip; C > 1 reuses each pass-1 partner
+// block C times; R >= 4 keeps several chunks (and their items) in flight.
+LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half) {
     LargeCfg c;
-    const int h = N - kTileBits;
-    const double per_x = (double)elem_bytes * (double)(1ull << N);
-    // ring of R slots of C shifts each, sized to stay within ~3/8 of L2
-    const double budget = std::max(16.0 * (1 << 20), 0.375 * (double)dev.l2_bytes);
-    c.R = 3;
-    int C_log = 0;
-    while (C_log < kTileBits && per_x * (double)(2 << C_log) * c.R <= budget) ++C_log;
+    const int h2 = N - kTileBits - half;
+    const double per_x = (double)elem_bytes * (double)(1ull << (N - half));
+    const double budget = std::max(24.0 * (1 << 20), 0.45 * (double)dev.l2_bytes);
+    int C_log = 3;
+    int R = 0;
+    for (; C_log >= 0; --C_log) {
+        R = (int)(budget / (per_x * (double)(1 << C_log)));
+        if (R >= 4) break;
+    }
+    if (C_log < 0) C_log = 0;
     c.C_log = C_log;
-    c.G2_log = std::min(C_log, h);
+    c.R = std::min(16, std::max(2, R));
+    c.D = std::max(1, c.R / 2);
+    c.G2_log = std::min(C_log, h2);
     const int occ = elem_bytes == 8 ? 2 : 1;
     c.grid = std::max(1, dev.sms * occ);
     return c;
 }
 
 size_t workspace_scratch_bytes(const DeviceInfo &dev, int N_max, int elem_bytes, sre_mode_t mode) {
+    (void)mode;
     if (N_max <= kTileBits) return 0;
-    const LargeCfg c = choose_large_cfg(dev, N_max, elem_bytes, mode);
-    return (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)elem_bytes << N_max);
+    size_t b = 0;
+    for (int half = 0; half <= 1; ++half) {
+        const LargeCfg c = choose_large_cfg(dev, N_max, elem_bytes, half);
+        b = std::max(b, (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)elem_bytes << (N_max - half)));
+    }
+    return b;
 }
 
 void workspace_free(Workspace *ws) {
@@ -390,6 +467,7 @@ void workspace_free(Workspace *ws) {
 
 cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int elem_bytes,
                             sre_mode_t mode) {
+    (void)mode;
     *ws = Workspace();
     ws->N_max = N_max;
     ws->elem_bytes = elem_bytes;
@@ -406,19 +484,25 @@ cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int
     SRE_TRY(cudaMalloc(&ws->flags, sizeof(int)));
     ws->part_cap = std::max(1, dev.sms * 4);
     SRE_TRY(cudaMalloc(&ws->part, sizeof(double) * ws->part_cap));
-    SRE_TRY(cudaMalloc(&ws->work, sizeof(unsigned long long)));
+    SRE_TRY(cudaMalloc(&ws->work, sizeof(unsigned long long) * 2));
     SRE_TRY(cudaMalloc(&ws->status, sizeof(int)));
     SRE_TRY(cudaMalloc(&ws->result, sizeof(Result)));
     if (N_max > kTileBits) {
-        // sizes for the largest N; smaller N reuse the same buffers
+        // sizes for every N up to N_max; both halves of the shift range
         size_t scratch = 0, item_cap = 0, chunk_cap = 0;
         for (int n = kTileBits + 1; n <= N_max; ++n) {
-            const LargeCfg c = choose_large_cfg(dev, n, elem_bytes, mode);
-            const int h = n - kTileBits;
-            scratch = std::max(scratch, (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)elem_bytes << n));
-            const size_t P2 = ((size_t)1 << c.C_log) << (h - c.G2_log);
-            item_cap = std::max(item_cap, (size_t)c.R * P2);
-            chunk_cap = std::max(chunk_cap, ((size_t)1 << n) >> c.C_log);
+            size_t chunks = 0;
+            for (int half = 0; half <= 1; ++half) {
+                const LargeCfg c = choose_large_cfg(dev, n, elem_bytes, half);
+                const int h2 = n - kTileBits - half;
+                scratch = std::max(scratch, (size_t)c.R * ((size_t)1 << c.C_log) *
+                                                ((size_t)elem_bytes << (n - half)));
+                const size_t P2 = ((size_t)1 << c.C_log) << (h2 - c.G2_log);
+                item_cap = std::max(item_cap, (size_t)c.R * P2);
+                const size_t span = half ? ((size_t)1 << n) - (size_t)kTile : (size_t)kTile;
+                chunks += (span >> c.C_log) + 2;
+            }
+            chunk_cap = std::max(chunk_cap, chunks);
         }
         ws->scratch_bytes = scratch;
         ws->item_part_cap = item_cap;
@@ -464,26 +548,67 @@ static cudaError_t launch_small(int N, const void *psi, uint64_t xb, uint64_t xe
     }
 }
 
-template <typename R, int H>
+template <typename R, int H2, bool HALF>
 static cudaError_t launch_large_h(const LargeArgs &a, int grid, cudaStream_t st) {
     const size_t smem = tile_smem_bytes(sizeof(v2_t<R>));
-    auto kern = k_large<R, H>;
+    auto kern = k_large<R, H2, HALF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename R>
+template <typename R, bool HALF>
 static cudaError_t launch_large(const LargeArgs &a, int grid, cudaStream_t st) {
-    switch (a.h) {
+    switch (a.h2) {
 #define SRE_CASE(n) \
-    case n: return launch_large_h<R, n>(a, grid, st);
-        SRE_CASE(1) SRE_CASE(2) SRE_CASE(3) SRE_CASE(4) SRE_CASE(5) SRE_CASE(6)
+    case n: return launch_large_h<R, n, HALF>(a, grid, st);
+        SRE_CASE(0) SRE_CASE(1) SRE_CASE(2) SRE_CASE(3) SRE_CASE(4) SRE_CASE(5) SRE_CASE(6)
         SRE_CASE(7) SRE_CASE(8) SRE_CASE(9) SRE_CASE(10) SRE_CASE(11) SRE_CASE(12)
 #undef SRE_CASE
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Fill LargeArgs for the shift range [xb, xe) (all of it halved or not).
+static cudaError_t make_large_args(LargeArgs *a, const Workspace &ws, const DeviceInfo &dev,
+                                   const void *psi, int N, uint64_t xb, uint64_t xe, int half,
+                                   int elem_bytes, size_t chunk_off, double *per_x,
+                                   long long wait_ns, const LargeCfg *ovr, int *grid) {
+    const LargeCfg c = ovr ? *ovr : choose_large_cfg(dev, N, elem_bytes, half);
+    LargeArgs &A = *a;
+    A.psi = psi;
+    A.N = N;
+    A.half = half;
+    A.h2 = N - kTileBits - half;
+    A.x_begin = xb;
+    A.x_end = xe;
+    A.C_log = c.C_log;
+    A.R = c.R;
+    A.G2_log = std::min(c.G2_log, A.h2);
+    A.x0 = xb & ~((1ull << c.C_log) - 1);
+    A.n_chunks = (long long)((xe - A.x0 + (1ull << c.C_log) - 1) >> c.C_log);
+    A.D = (int)std::max<long long>(1, std::min<long long>(std::min(c.D, c.R - 1), A.n_chunks));
+    if (A.R < 2) return cudaErrorInvalidValue;
+    A.P1 = 1 << A.h2;
+    A.P2 = (1 << c.C_log) << (A.h2 - A.G2_log);
+    A.n_items = A.n_chunks * (long long)(A.P1 + A.P2);
+    const size_t need_scratch = (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)elem_bytes << (N - half));
+    if (need_scratch > ws.scratch_bytes || chunk_off + (size_t)A.n_chunks > ws.chunk_cap ||
+        (size_t)c.R * A.P2 > ws.item_part_cap)
+        return cudaErrorInvalidValue;
+    A.scratch = ws.scratch;
+    A.item_part = ws.item_part;
+    A.chunk_sum = ws.chunk_sum + chunk_off;
+    A.done1 = ws.counters + chunk_off;
+    A.done2 = ws.counters + ws.chunk_cap + chunk_off;
+    A.freed = ws.counters + 2 * ws.chunk_cap + chunk_off;
+    A.work = ws.work + (half ? 1 : 0);
+    A.per_x = per_x;
+    A.status = ws.status;
+    A.wait_ns = wait_ns;
+    *grid = (int)std::max<long long>(1, std::min<long long>(c.grid, A.n_items));
+    return cudaSuccess;
 }
 
 cudaError_t enqueue_copy_sums(const Workspace &ws, double *d_out2, cudaStream_t stream) {
@@ -515,47 +640,37 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
         parts = ws.part;
         nparts = np;
     } else {
-        LargeCfg c = cfg_override ? *cfg_override : choose_large_cfg(dev, N, sizeof(v2_t<R>),
-                                                                     SRE_MODE_FP32);
-        LargeArgs a;
-        a.psi = psi;
-        a.N = N;
-        a.h = N - kTileBits;
-        a.x_begin = x_begin;
-        a.x_end = x_end;
-        a.C_log = c.C_log;
-        a.R = c.R;
-        a.G2_log = std::min(c.G2_log, a.h);
-        a.x0 = x_begin & ~((1ull << c.C_log) - 1);
-        a.n_chunks = (long long)((x_end - a.x0 + (1ull << c.C_log) - 1) >> c.C_log);
-        a.P1 = 1 << a.h;
-        a.P2 = (1 << c.C_log) << (a.h - a.G2_log);
-        a.n_items = a.n_chunks * (long long)(a.P1 + a.P2);
-        const size_t need_scratch = (size_t)c.R * ((size_t)1 << c.C_log) * (sizeof(v2_t<R>) << N);
-        if (need_scratch > ws.scratch_bytes || (size_t)a.n_chunks > ws.chunk_cap ||
-            (size_t)c.R * a.P2 > ws.item_part_cap)
-            return cudaErrorInvalidValue;
-        a.scratch = ws.scratch;
-        a.item_part = ws.item_part;
-        a.chunk_sum = ws.chunk_sum;
-        a.done1 = ws.counters;
-        a.done2 = ws.counters + ws.chunk_cap;
-        a.freed = ws.counters + 2 * ws.chunk_cap;
-        a.work = ws.work;
-        a.per_x = d_per_x;
-        a.status = ws.status;
-        a.wait_ns = wait_ns;
+        // shifts below 4096 (pivot bit inside the 12-bit block): full
+        // transform; shifts from 4096 up: conjugate-symmetry halving
+        const int eb = (int)sizeof(v2_t<R>);
+        const uint64_t split = std::min<uint64_t>(std::max<uint64_t>(x_begin, kTile), x_end);
         if ((e = cudaMemsetAsync(ws.counters, 0, sizeof(unsigned) * 3 * ws.chunk_cap, st)) != cudaSuccess)
             return e;
-        if ((e = cudaMemsetAsync(ws.work, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-        const int grid = (int)std::max<long long>(1, std::min<long long>(c.grid, a.n_items));
+        if ((e = cudaMemsetAsync(ws.work, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess) return e;
+        size_t chunks = 0;
         if (ws.ev_begin && (e = cudaEventRecord(ws.ev_begin, st)) != cudaSuccess) return e;
-        if ((e = launch_large<R>(a, grid, st)) != cudaSuccess) return e;
+        for (int half = 0; half <= 1; ++half) {
+            const uint64_t xb = half ? split : x_begin;
+            const uint64_t xe = half ? x_end : split;
+            if (xb >= xe) continue;
+            LargeArgs a;
+            int grid = 0;
+            if ((e = make_large_args(&a, ws, dev, psi, N, xb, xe, half, eb, chunks,
+                                     d_per_x ? d_per_x + (xb - x_begin) : nullptr, wait_ns,
+                                     cfg_override && half ? cfg_override : nullptr, &grid)) != cudaSuccess)
+                return e;
+            if (half)
+                e = launch_large<R, true>(a, grid, st);
+            else
+                e = launch_large<R, false>(a, grid, st);
+            if (e != cudaSuccess) return e;
+            ws.launches += 1;
+            chunks += (size_t)a.n_chunks;
+        }
         if (ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
         ws.main_kernel = "k_large";
-        ws.launches += 1;
         parts = ws.chunk_sum;
-        nparts = a.n_chunks;
+        nparts = (long long)chunks;
     }
     k_finalize<<<1, kFinalThreads, 0, st>>>(parts, nparts, ws.npart, kNormBlocks, N, ws.flags,
                                             ws.status, ws.result, d_m2);

@@ -77,13 +77,16 @@ __device__ __forceinline__ void relayout(R (&re)[16], R (&im)[16], v2_t<R> *buf,
     }
 }
 
-// Transform over tile bits [0, NB), 1 <= NB <= 12.  Input in round-0
-// layout; output in round-((NB-1)/4) layout.  Uses bufA (NB > 4) and bufB
-// (NB > 8); the caller synchronises before reusing a buffer it shares.
+// Transform over tile bits [0, NB), 0 <= NB <= 12.  Input in round-0
+// layout; output in round-(max(NB-1,0)/4) layout.  Uses bufA (NB > 4) and
+// bufB (NB > 8).  Each relayout ends with every thread past a barrier that
+// follows all reads of the previous relayout's buffer, so consecutive calls
+// need no extra barrier when NB > 8; with one relayout (4 < NB <= 8) the
+// caller alternates bufA between two buffers from call to call.
 template <int NB, typename R>
 __device__ __forceinline__ void tile_fwht(R (&re)[16], R (&im)[16], v2_t<R> *bufA,
                                           v2_t<R> *bufB, int tid) {
-    static_assert(NB >= 1 && NB <= 12, "tile transform covers 1..12 bits");
+    static_assert(NB >= 0 && NB <= 12, "tile transform covers 0..12 bits");
     reg_stages<0, NB>(re, im);
     if constexpr (NB > 4) {
         relayout<0>(re, im, bufA, tid);
@@ -96,6 +99,18 @@ __device__ __forceinline__ void tile_fwht(R (&re)[16], R (&im)[16], v2_t<R> *buf
 }
 
 template <int NB> struct FinalRound { static constexpr int value = (NB - 1) / 4; };
+
+// sum_i (Re F_i)^4 + (Im F_i)^4 over the thread's 16 entries, in R.
+template <typename R>
+__device__ __forceinline__ R sum_re4_im4(const R (&re)[16], const R (&im)[16]) {
+    R s = R(0);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const R a = re[i] * re[i], b = im[i] * im[i];
+        s += a * a + b * b;
+    }
+    return s;
+}
 
 // sum_i |F_i|^4 over the thread's 16 entries, in R.
 template <typename R>

@@ -115,7 +115,9 @@ def test_per_shift_sums(sre, torch_cuda, N):
             out, px = p.sum4_range(dev(torch_cuda, psi), 0, 1 << N, per_x=True)
             torch_cuda.cuda.synchronize()
         np.testing.assert_allclose(px.cpu().numpy(), ref, rtol=0, atol=rtol * ref.max())
-        assert out[1].item() == pytest.approx(oracle.norm2(psi), rel=1e-12)
+        # FP32 mode evaluates the state rounded to complex64
+        n2 = oracle.norm2(psi if mode == "fp64" else psi.astype(np.complex64))
+        assert out[1].item() == pytest.approx(n2, rel=1e-12)
 
 
 @pytest.mark.parametrize("N,ranges", [(9, [(0, 5), (5, 300), (300, 512)]),
@@ -166,7 +168,7 @@ def test_n20_full_size_sampled(sre, torch_cuda):
     sample = sorted(set([0, 1, 4095, 4096, (1 << N) - 1] + list(rng.integers(0, 1 << N, 27))))
     for x in sample:
         ref = oracle.sum4_xorfwht(psi, int(x), int(x) + 1)
-        assert abs(px[x] - ref) <= 2e-6 * max(ref, px.max() * 1e-3), (x, px[x], ref)
+        assert abs(px[x] - ref) <= 1e-5 * ref, (x, px[x], ref)
     # Haar states concentrate: 2^-M2 = S/(d n2^4) within a few percent of 4/(d+3)
     assert abs(2.0 ** (-m2) / (4 / ((1 << N) + 3)) - 1) < 0.05
 

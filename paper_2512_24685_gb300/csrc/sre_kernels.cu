@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
         }
         tile_fwht<NB>(re, im, bufA, bufB, tid);
         acc += (double)sum_abs4(re, im);
-        __syncthreads();
+        __syncthreads();  // bufB is reused by the next tile
     }
     const double s = block_sum(acc, red);
     if (tid == 0) part[blockIdx.x] = s;
@@ -214,12 +214,13 @@ template <typename R, int H2, bool HALF>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(LargeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = v2_t<R>;
-    V *tileS = reinterpret_cast<V *>(smem_raw);  // partner block (pass 1)
-    V *bufA = tileS + kTile;
-    V *bufB = bufA + kTile;
+    V *bufA = reinterpret_cast<V *>(smem_raw);  // warp-local round 0 -> 1 moves
+    V *bufB = bufA + kTile;                      // round 1 -> 2 moves, alternating
+    V *bufC = bufB + kTile;                      //   with bufC from tile to tile
     __shared__ double red[kThreads / 32];
     __shared__ long long s_item;
     __shared__ int s_flag;
+    unsigned tcount = 0;  // tiles that used a round 1 -> 2 move (uniform)
 
     const int tid = threadIdx.x;
     const int lgx = a.N - (HALF ? 1 : 0);        // log2 scratch entries per shift
@@ -258,37 +259,48 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
             if (!s_flag) break;
             const uint64_t xh = xc >> kTileBits;
             const int xl0 = (int)(xc & (kTile - 1));
-            const V *pb = psi + (((uint64_t)th ^ xh) << kTileBits);
-            for (int j = tid; j < kTile; j += kThreads) tileS[swz(j)] = pb[j];
+            // Round-2 layout: thread tid holds t_l = i << 8 | tid of block th
+            // (own factors phi_t in registers); its partners t ^ x are
+            // t_l ^ xlow of block th ^ x_h, read coalesced (each warp load
+            // covers one aligned 256-entry run).
             R ar[16], ai[16];
-            const V *pa = psi + ((uint64_t)th << kTileBits) + (tid << 4);
+            {
+                const V *pa = psi + ((uint64_t)th << kTileBits) + tid;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const V v = pa[i];
-                ar[i] = v.x;
-                ai[i] = v.y;
+                for (int i = 0; i < 16; ++i) {
+                    const V va = __ldg(pa + (i << 8));
+                    ar[i] = va.x;
+                    ai[i] = va.y;
+                }
             }
-            __syncthreads();
+            const V *pb = psi + (((uint64_t)th ^ xh) << kTileBits);
             for (int xl = 0; xl < C; ++xl) {
                 const uint64_t x = xc + (uint64_t)xl;
                 if (x < a.x_begin || x >= a.x_end) continue;
                 const int xlow = xl0 + xl;
+                const V *pbx = pb + (tid ^ (xlow & 255));
+                const int q = xlow >> 8;
                 R re[16], im[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    const V b = tileS[swz(elem<0>(tid, i) ^ xlow)];
+                    const V b = __ldg(pbx + ((i ^ q) << 8));
                     // conj(phi_{t^x}) * phi_t
                     re[i] = b.x * ar[i] + b.y * ai[i];
                     im[i] = b.x * ai[i] - b.y * ar[i];
                 }
-                tile_fwht<kTileBits>(re, im, bufA, bufB, tid);
-                V *o = slot_base + ((size_t)xl << lgx) + ((size_t)tp << kTileBits);
+                V *bB = (tcount & 1) ? bufC : bufB;
+                ++tcount;
+                tile_fwht12_rev(re, im, bufA, bB, tid);
+                // output in round-0 layout (z_l = 16 tid + i) stored at the
+                // bit-permuted position i << 8 | tid: coalesced stores; pass 2
+                // only sums over z, so the order of z inside a block is free
+                V *o = slot_base + ((size_t)xl << lgx) + ((size_t)tp << kTileBits) + tid;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     V v;
                     v.x = re[i];
                     v.y = im[i];
-                    __stcg(o + elem<2>(tid, i), v);
+                    __stcg(o + (i << 8), v);
                 }
             }
             __syncthreads();
@@ -321,9 +333,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
                         re[i] = v.x;
                         im[i] = v.y;
                     }
-                    // one relayout: alternate buffers between consecutive tiles
-                    V *b0 = (H2 > 4 && H2 <= 8 && (gb & 1)) ? bufB : bufA;
-                    tile_fwht<H2>(re, im, b0, bufB, tid);
+                    V *bB = (tcount & 1) ? bufC : bufB;
+                    if (H2 > 8) ++tcount;
+                    tile_fwht<H2>(re, im, bufA, bB, tid);
                     if (HALF)
                         acc += 16.0 * (double)sum_re4_im4(re, im);
                     else

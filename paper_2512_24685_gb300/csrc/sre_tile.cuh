@@ -58,44 +58,68 @@ __device__ __forceinline__ void reg_stages(R (&re)[16], R (&im)[16]) {
     }
 }
 
-// Move the tile from round-K layout to round-(K+1) layout through `buf`.
-template <int K, typename R>
+// Move the tile from round-KA layout to round-KB layout through `buf`.
+// Moves between rounds 0 and 1 exchange register bits with thread bits 0-3,
+// i.e. data moves only inside groups of 16 threads of one warp and each warp
+// touches only its own 512-entry part of the buffer: they are ordered with
+// __syncwarp (WARP = true).  Moves between rounds 1 and 2 exchange with
+// thread bits 4-7 (across warps) and need a CTA barrier; their buffer must
+// not be the one the previous tile's cross-warp move read (callers
+// alternate two buffers).
+template <int KA, int KB, bool WARP, typename R>
 __device__ __forceinline__ void relayout(R (&re)[16], R (&im)[16], v2_t<R> *buf, int tid) {
+    if (WARP) __syncwarp();
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         v2_t<R> v;
         v.x = re[i];
         v.y = im[i];
-        buf[swz(elem<K>(tid, i))] = v;
+        buf[swz(elem<KA>(tid, i))] = v;
     }
-    __syncthreads();
+    if (WARP)
+        __syncwarp();
+    else
+        __syncthreads();
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const v2_t<R> v = buf[swz(elem<K + 1>(tid, i))];
+        const v2_t<R> v = buf[swz(elem<KB>(tid, i))];
         re[i] = v.x;
         im[i] = v.y;
     }
 }
 
-// Transform over tile bits [0, NB), 0 <= NB <= 12.  Input in round-0
-// layout; output in round-(max(NB-1,0)/4) layout.  Uses bufA (NB > 4) and
-// bufB (NB > 8).  Each relayout ends with every thread past a barrier that
-// follows all reads of the previous relayout's buffer, so consecutive calls
-// need no extra barrier when NB > 8; with one relayout (4 < NB <= 8) the
-// caller alternates bufA between two buffers from call to call.
+// Transform over tile bits [0, NB), 0 <= NB <= 12, bits 0-3 first.  Input in
+// round-0 layout; output in round-(max(NB-1,0)/4) layout.  bufA serves the
+// warp-local round 0 -> 1 move (consecutive calls may share it); bufB the
+// CTA-wide round 1 -> 2 move (NB > 8): consecutive calls must alternate bufB
+// between two buffers.
 template <int NB, typename R>
 __device__ __forceinline__ void tile_fwht(R (&re)[16], R (&im)[16], v2_t<R> *bufA,
                                           v2_t<R> *bufB, int tid) {
     static_assert(NB >= 0 && NB <= 12, "tile transform covers 0..12 bits");
     reg_stages<0, NB>(re, im);
     if constexpr (NB > 4) {
-        relayout<0>(re, im, bufA, tid);
+        relayout<0, 1, true>(re, im, bufA, tid);
         reg_stages<1, NB>(re, im);
     }
     if constexpr (NB > 8) {
-        relayout<1>(re, im, bufB, tid);
+        relayout<1, 2, false>(re, im, bufB, tid);
         reg_stages<2, NB>(re, im);
     }
+}
+
+// Full 12-bit transform, bits 8-11 first: input in round-2 layout (thread
+// tid holds e = i << 8 | tid, so loads of consecutive threads are
+// contiguous), output in round-0 layout.  One CTA-wide move (bufB, to be
+// alternated between consecutive calls) and one warp-local move (bufA).
+template <typename R>
+__device__ __forceinline__ void tile_fwht12_rev(R (&re)[16], R (&im)[16], v2_t<R> *bufA,
+                                                v2_t<R> *bufB, int tid) {
+    reg_stages<2, 12>(re, im);
+    relayout<2, 1, false>(re, im, bufB, tid);
+    reg_stages<1, 12>(re, im);
+    relayout<1, 0, true>(re, im, bufA, tid);
+    reg_stages<0, 12>(re, im);
 }
 
 template <int NB> struct FinalRound { static constexpr int value = (NB - 1) / 4; };

@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -226,6 +227,11 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     plan = binding.Plan(N, "c64", args.mode)
+    tuning, tune_ms = None, None
+    if N > 12 and not args.no_autotune:
+        tuning, tune_ms = plan.autotune(N)
+    elif N > 12:
+        tuning = plan.get_tuning(N)
     plan.set_profiling(True)
 
     def barrier():
@@ -341,7 +347,8 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"N={N} Haar-random state (complex64), all 4^{N} Pauli strings per step",
                    "N": N, "states_per_gpu": 1, "mode": args.mode, "l2_flush": "512 MiB write between steps",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "tuning": tuning,
+                   "autotune_slice_ms": tune_ms},
         "m2": m2_val, "states_per_s": world * args.steps / elapsed_s,
         "gpu_launches": int(launches), "wall_s": wall,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -110,6 +110,37 @@ SRE_API sre_status_t sre_plan_create(int N, sre_dtype_t dtype, sre_plan_t *out);
 SRE_API sre_status_t sre_plan_set_mode(sre_plan_t plan, sre_mode_t mode);
 SRE_API sre_status_t sre_plan_get_mode(sre_plan_t plan, sre_mode_t *mode);
 
+/*
+ * Tuning of the two-pass kernel used for N > 12 (one pass transforms the
+ * low 12 bits of t per block into an L2-resident ring of scratch, the other
+ * the remaining bits).  x_batch_log: log2 of the shifts that share one
+ * pass-1 partner block (0..3); ring_slots: chunks held in the ring (>= 2);
+ * lag: how many chunks pass 2 trails pass 1 (1 <= lag < ring_slots);
+ * pass2_tiles_log: log2 of the 2^12-entry tiles per pass-2 work item.
+ * A value of -1 keeps the library's choice for that field; all -1 restores
+ * the defaults.  The scratch ring must fit the plan's allocation
+ * (SRE_EINVAL otherwise).  Applies to the halved shifts (x >= 4096).
+ */
+typedef struct {
+    int x_batch_log;
+    int ring_slots;
+    int lag;
+    int pass2_tiles_log;
+} sre_tuning_t;
+SRE_API sre_status_t sre_plan_set_tuning(sre_plan_t plan, const sre_tuning_t *tuning);
+SRE_API sre_status_t sre_plan_get_tuning(sre_plan_t plan, int N, sre_tuning_t *tuning);
+
+/*
+ * Autotuner: for the plan's mode and the given N (> 12), time a fixed set of
+ * candidate tunings on a bounded slice of shifts of a synthetic state held in
+ * the plan, keep the fastest and make it the plan's tuning for that N.
+ * SYNCHRONOUS (uses `stream`).  *best receives the chosen tuning and *ms its
+ * time on the slice (either may be NULL).  N <= 12 has nothing to tune
+ * (SRE_OK, tuning left unchanged).
+ */
+SRE_API sre_status_t sre_plan_autotune(sre_plan_t plan, int N, sre_stream_t stream,
+                                       sre_tuning_t *best, double *ms);
+
 /* Profiling support.  When enabled (enable != 0), the plan records two CUDA
  * events on the stream around the main transform kernel of each evaluation;
  * sre_plan_last_kernel_ms waits for the second event and returns the

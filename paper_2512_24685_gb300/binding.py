@@ -52,6 +52,14 @@ class SreError(RuntimeError):
         super().__init__(f"{where}: {name}: {msg}{extra}")
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("x_batch_log", ctypes.c_int), ("ring_slots", ctypes.c_int), ("lag", ctypes.c_int),
+                ("pass2_tiles_log", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ServerCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
                 ("max_queue", ctypes.c_int), ("max_N", ctypes.c_int), ("mode", ctypes.c_int),
@@ -85,6 +93,9 @@ def _declare(lib):
         "sre_plan_set_profiling": (S, [_vp, _i]),
         "sre_plan_last_kernel_ms": (S, [_vp, _dp, ctypes.POINTER(ctypes.c_char_p)]),
         "sre_plan_launch_count": (S, [_vp, ctypes.POINTER(_u64)]),
+        "sre_plan_set_tuning": (S, [_vp, ctypes.POINTER(Tuning)]),
+        "sre_plan_get_tuning": (S, [_vp, _i, ctypes.POINTER(Tuning)]),
+        "sre_plan_autotune": (S, [_vp, _i, _vp, ctypes.POINTER(Tuning), _dp]),
         "sre_m2": (S, [_vp, _vp, _i, _vp, _dp]),
         "sre_m2_async": (S, [_vp, _vp, _i, _vp, _vp]),
         "sre_m2_host": (S, [_vp, _vp, _i, _vp, _dp]),
@@ -196,6 +207,24 @@ class Plan:
         _check(load_library().sre_plan_last_kernel_ms(self._h, ctypes.byref(ms), ctypes.byref(name)),
                "sre_plan_last_kernel_ms")
         return ms.value, (name.value or b"").decode()
+
+    def set_tuning(self, x_batch_log=-1, ring_slots=-1, lag=-1, pass2_tiles_log=-1):
+        """sre_plan_set_tuning: override two-pass fields (-1 = library choice)."""
+        t = Tuning(int(x_batch_log), int(ring_slots), int(lag), int(pass2_tiles_log))
+        _check(load_library().sre_plan_set_tuning(self._h, ctypes.byref(t)), "sre_plan_set_tuning")
+
+    def get_tuning(self, N: int) -> dict:
+        t = Tuning()
+        _check(load_library().sre_plan_get_tuning(self._h, int(N), ctypes.byref(t)), "sre_plan_get_tuning")
+        return t.as_dict()
+
+    def autotune(self, N: int | None = None, stream=None):
+        """sre_plan_autotune: (best tuning dict, ms on the timing slice)."""
+        t, ms = Tuning(), ctypes.c_double()
+        _check(load_library().sre_plan_autotune(self._h, int(self.N if N is None else N),
+                                                _stream_handle(stream), ctypes.byref(t),
+                                                ctypes.byref(ms)), "sre_plan_autotune")
+        return t.as_dict(), ms.value
 
     def launch_count(self) -> int:
         c = ctypes.c_uint64()

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "sre_batched.h"
 #include "sre_internal.h"
@@ -44,6 +45,10 @@ struct sre_plan_s {
     sre::BatchedContext *batched = nullptr;
     bool profiling = false;
     unsigned long long extra_launches = 0;  // launches of workspaces that were freed
+    sre_tuning_t user = {-1, -1, -1, -1};           // sre_plan_set_tuning
+    sre::LargeCfg tuned[SRE_MAX_QUBITS + 1];        // sre_plan_autotune results
+    bool has_tuned[SRE_MAX_QUBITS + 1] = {};
+    void *tune_state = nullptr;                     // synthetic state for autotuning
 };
 
 namespace {
@@ -197,20 +202,152 @@ sre_status_t sre_plan_destroy(sre_plan_t p) {
     sre::workspace_free(&p->ws);
     cudaFreeHost(p->h_result);
     cudaFree(p->d_stage);
+    cudaFree(p->tune_state);
     delete p;
     return SRE_OK;
 }
 
+// Configuration of the halved shifts for N > 12: the library default, then
+// the autotuned one, then the caller's explicit fields.
+static sre::LargeCfg plan_cfg(sre_plan_t p, int N) {
+    const int eb = elem_bytes_for_mode(p->mode);
+    sre::LargeCfg c = p->has_tuned[N] ? p->tuned[N] : sre::choose_large_cfg(p->dev, N, eb, 1);
+    if (p->user.x_batch_log >= 0) c.C_log = p->user.x_batch_log;
+    if (p->user.ring_slots >= 0) c.R = p->user.ring_slots;
+    if (p->user.lag >= 0) c.D = p->user.lag;
+    if (p->user.pass2_tiles_log >= 0) c.G2_log = p->user.pass2_tiles_log;
+    c.G2_log = std::min(c.G2_log, N - sre::kTileBits - 1);
+    return c;
+}
+
+static sre_status_t enqueue_plan_cfg(sre_plan_t p, const void *d_state, int N, uint64_t xb,
+                                     uint64_t xe, cudaStream_t st, double *d_m2, double *d_per_x,
+                                     sre::LargeCfg *cfg);
+
 static sre_status_t enqueue_plan(sre_plan_t p, const void *d_state, int N, uint64_t xb, uint64_t xe,
                                  cudaStream_t st, double *d_m2, double *d_per_x) {
+    sre::LargeCfg c;
+    sre::LargeCfg *cp = nullptr;
+    if (N > sre::kTileBits) {
+        c = plan_cfg(p, N);
+        if (!sre::large_cfg_fits(p->ws, c, N, 1)) return SRE_EINVAL;
+        cp = &c;
+    }
+    return enqueue_plan_cfg(p, d_state, N, xb, xe, st, d_m2, d_per_x, cp);
+}
+
+static sre_status_t enqueue_plan_cfg(sre_plan_t p, const void *d_state, int N, uint64_t xb,
+                                     uint64_t xe, cudaStream_t st, double *d_m2, double *d_per_x,
+                                     sre::LargeCfg *cfg) {
     cudaError_t e;
     if (sre::tc_mode_available(p->mode) && p->mode != SRE_MODE_FP32 && p->mode != SRE_MODE_FP64)
         e = sre::tc_enqueue_m2(p->ws, p->dev, d_state, p->dtype, N, xb, xe, p->mode, st, d_m2,
                                d_per_x, p->wait_ns);
     else
         e = sre::enqueue_m2(p->ws, p->dev, d_state, p->dtype, N, xb, xe, p->mode, st, d_m2,
-                            d_per_x, p->wait_ns, nullptr);
+                            d_per_x, p->wait_ns, cfg);
     return e == cudaSuccess ? SRE_OK : cuda_fail(e);
+}
+
+sre_status_t sre_plan_set_tuning(sre_plan_t p, const sre_tuning_t *t) {
+    if (!p || !t) return SRE_EINVAL;
+    if (t->x_batch_log > 3 || t->ring_slots > sre::kMaxRing || (t->ring_slots >= 0 && t->ring_slots < 2) ||
+        (t->lag >= 0 && t->lag < 1) || t->pass2_tiles_log > 12)
+        return SRE_EINVAL;
+    p->user = *t;
+    return SRE_OK;
+}
+
+sre_status_t sre_plan_get_tuning(sre_plan_t p, int N, sre_tuning_t *t) {
+    if (!p || !t || N < 1 || N > p->N) return SRE_EINVAL;
+    if (N <= sre::kTileBits) {
+        *t = {-1, -1, -1, -1};
+        return SRE_OK;
+    }
+    const sre::LargeCfg c = plan_cfg(p, N);
+    t->x_batch_log = c.C_log;
+    t->ring_slots = c.R;
+    t->lag = c.D;
+    t->pass2_tiles_log = c.G2_log;
+    return SRE_OK;
+}
+
+sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tuning_t *best,
+                               double *ms_out) {
+    if (!p || N < 1 || N > p->N) return SRE_EINVAL;
+    if (N <= sre::kTileBits) return SRE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (!p->tune_state) {
+        e = cudaMalloc(&p->tune_state, (size_t)dtype_bytes(p->dtype) << p->N);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if ((e = sre::enqueue_fill_synthetic(p->tune_state, N, p->dtype, st)) != cudaSuccess) return cuda_fail(e);
+    // candidates around the in-flight estimate: chunk size, lag depth, pass-2 item size
+    const int eb = elem_bytes_for_mode(p->mode);
+    const sre::LargeCfg base = sre::choose_large_cfg(p->dev, N, eb, 1);
+    const int h2 = N - sre::kTileBits - 1;
+    const int inflight = std::max(1, (base.grid + (1 << h2) - 1) >> h2);
+    std::vector<sre::LargeCfg> cands;
+    for (int C_log = 0; C_log <= 3; ++C_log)
+        for (int dm = 1; dm <= 2; ++dm)
+            for (int g = 0; g <= 1; ++g) {
+                sre::LargeCfg c = base;
+                c.C_log = C_log;
+                c.D = std::min(dm * inflight + 1, sre::kMaxRing / 2 - 1);
+                c.R = 2 * c.D + 1;
+                c.G2_log = g ? std::min(C_log, h2) : 0;
+                if (g == 0 && std::min(C_log, h2) == 0) continue;  // same as g = 1
+                if (sre::large_cfg_fits(p->ws, c, N, 1)) cands.push_back(c);
+            }
+    if (cands.empty()) return SRE_OK;
+    // a slice of halved shifts worth ~2^34 entries of work
+    const uint64_t d = 1ull << N;
+    uint64_t n = std::max<uint64_t>(4096, (N < 34 ? (1ull << (34 - N)) : 1));
+    n = std::min<uint64_t>(n, d / 2);
+    const uint64_t xb = d / 2, xe = xb + n;
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e);
+    }
+    double best_ms = 1e30;
+    sre::LargeCfg best_c = base;
+    sre_status_t s = SRE_OK;
+    for (sre::LargeCfg &c : cands) {
+        float ms = 0.f, ms_min = 1e30f;
+        for (int rep = 0; rep < 3 && s == SRE_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            s = enqueue_plan_cfg(p, p->tune_state, N, xb, xe, st, nullptr, nullptr, &c);
+            cudaEventRecord(e1, st);
+            if (s != SRE_OK) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                s = cuda_fail(e);
+                break;
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_min = std::min(ms_min, ms);
+        }
+        if (s != SRE_OK) break;
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != SRE_OK) return s;
+    p->tuned[N] = best_c;
+    p->has_tuned[N] = true;
+    if (best) {
+        best->x_batch_log = best_c.C_log;
+        best->ring_slots = best_c.R;
+        best->lag = best_c.D;
+        best->pass2_tiles_log = best_c.G2_log;
+    }
+    if (ms_out) *ms_out = best_ms;
+    return SRE_OK;
 }
 
 static sre_status_t read_result(sre_plan_t p, cudaStream_t st, double *m2_host) {

@@ -14,6 +14,8 @@ constexpr int kThreads = 256;              // threads per tile CTA
 constexpr int kPerThread = kTile / kThreads;  // 16 entries per thread (4 register bits)
 constexpr int kNormBlocks = 264;           // fixed grid of the norm reduction
 constexpr int kFinalThreads = 256;
+constexpr int kMaxRing = 64;                      // ring slots a tuned configuration may use
+constexpr size_t kTuneScratch = (size_t)96 << 20;  // scratch floor for N > 12 plans
 
 // Device-side result block of one evaluation (written by the finalize kernel).
 struct Result {
@@ -75,6 +77,12 @@ cudaError_t query_device(DeviceInfo *info);
 // Pick the two-pass configuration for N > 12 (half: conjugate-symmetry halved
 // shifts, x >= 4096).
 LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half);
+
+// Does a (possibly tuned) configuration fit the workspace allocation?
+bool large_cfg_fits(const Workspace &ws, const LargeCfg &c, int N, int half);
+
+// Fill a state buffer with deterministic pseudo-random amplitudes (timing).
+cudaError_t enqueue_fill_synthetic(void *buf, int N, sre_dtype_t dtype, cudaStream_t st);
 
 // Bytes of workspace needed for states up to N_max with element size.
 size_t workspace_scratch_bytes(const DeviceInfo &dev, int N_max, int elem_bytes, sre_mode_t mode);

@@ -81,36 +81,33 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = v2_t<R>;
     V *psi_s = reinterpret_cast<V *>(smem_raw);
-    V *bufA = psi_s + kTile;
-    V *bufB = bufA + kTile;
+    V *bufA = psi_s + kTileSlots;
+    V *bufB = bufA + kTileSlots;
     __shared__ double red[kThreads / 32];
     constexpr int N = NB;
     constexpr int d = 1 << N;
     const int tid = threadIdx.x;
-    for (int t = tid; t < d; t += kThreads) psi_s[swz(t)] = psi[t];
+    for (int t = tid; t < d; t += kThreads) psi_s[pad(t)] = psi[t];
     __syncthreads();
 
     double acc = 0.0;
     for (long long g = blockIdx.x; g < ntiles; g += gridDim.x) {
-        R re[16], im[16];
+        cx_t<R> v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const uint64_t flat = ((uint64_t)g << kTileBits) | (uint64_t)elem<0>(tid, i);
             const uint64_t x = x_begin + (flat >> N);
             const int t = (int)(flat & (d - 1));
             if (x < x_end) {
-                const V a = psi_s[swz(t)];
-                const V b = psi_s[swz(t ^ (int)x)];
-                // conj(phi_{t^x}) * phi_t
-                re[i] = b.x * a.x + b.y * a.y;
-                im[i] = b.x * a.y - b.y * a.x;
+                const V a = psi_s[pad(t)];
+                const V b = psi_s[pad(t ^ (int)x)];
+                v[i] = conj_mul<R>(b.x, b.y, a.x, a.y);  // conj(phi_{t^x}) * phi_t
             } else {
-                re[i] = R(0);
-                im[i] = R(0);
+                v[i] = Cx<R>::zero();
             }
         }
-        tile_fwht<NB>(re, im, bufA, bufB, tid);
-        acc += (double)sum_abs4(re, im);
+        tile_fwht<NB, R>(v, bufA, bufB, tid);
+        acc += (double)sum_abs4<R>(v);
         __syncthreads();  // bufB is reused by the next tile
     }
     const double s = block_sum(acc, red);
@@ -215,8 +212,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = v2_t<R>;
     V *bufA = reinterpret_cast<V *>(smem_raw);  // warp-local round 0 -> 1 moves
-    V *bufB = bufA + kTile;                      // round 1 -> 2 moves, alternating
-    V *bufC = bufB + kTile;                      //   with bufC from tile to tile
+    V *bufB = bufA + kTileSlots;                 // round 1 -> 2 moves, alternating
+    V *bufC = bufB + kTileSlots;                 //   with bufC from tile to tile
     __shared__ double red[kThreads / 32];
     __shared__ long long s_item;
     __shared__ int s_flag;
@@ -280,28 +277,21 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
                 const int xlow = xl0 + xl;
                 const V *pbx = pb + (tid ^ (xlow & 255));
                 const int q = xlow >> 8;
-                R re[16], im[16];
+                cx_t<R> v[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const V b = __ldg(pbx + ((i ^ q) << 8));
-                    // conj(phi_{t^x}) * phi_t
-                    re[i] = b.x * ar[i] + b.y * ai[i];
-                    im[i] = b.x * ai[i] - b.y * ar[i];
+                    v[i] = conj_mul<R>(b.x, b.y, ar[i], ai[i]);  // conj(phi_{t^x}) * phi_t
                 }
                 V *bB = (tcount & 1) ? bufC : bufB;
                 ++tcount;
-                tile_fwht12_rev(re, im, bufA, bB, tid);
+                tile_fwht12_rev<R>(v, bufA, bB, tid);
                 // output in round-0 layout (z_l = 16 tid + i) stored at the
                 // bit-permuted position i << 8 | tid: coalesced stores; pass 2
                 // only sums over z, so the order of z inside a block is free
                 V *o = slot_base + ((size_t)xl << lgx) + ((size_t)tp << kTileBits) + tid;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    V v;
-                    v.x = re[i];
-                    v.y = im[i];
-                    __stcg(o + (i << 8), v);
-                }
+                for (int i = 0; i < 16; ++i) __stcg(o + (i << 8), Cx<R>::to(v[i]));
             }
             __syncthreads();
             if (tid == 0) {
@@ -323,26 +313,44 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
                 const V *xb = slot_base + ((size_t)xl << lgx);
                 for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
                     const int zb = zb0 + gb;
-                    R re[16], im[16];
+                    cx_t<R> v[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const int e = elem<0>(tid, i);
                         const int tp = e & ((1 << H2) - 1);
                         const int zs = e >> H2;
-                        const V v = __ldcg(xb + ((size_t)tp << kTileBits) + (zb << zsub_bits) + zs);
-                        re[i] = v.x;
-                        im[i] = v.y;
+                        v[i] = Cx<R>::from(
+                            __ldcg(xb + ((size_t)tp << kTileBits) + (zb << zsub_bits) + zs));
                     }
                     V *bB = (tcount & 1) ? bufC : bufB;
                     if (H2 > 8) ++tcount;
-                    tile_fwht<H2>(re, im, bufA, bB, tid);
+                    tile_fwht<H2, R>(v, bufA, bB, tid);
                     if (HALF)
-                        acc += 16.0 * (double)sum_re4_im4(re, im);
+                        acc += 16.0 * (double)sum_re4_im4<R>(v);
                     else
-                        acc += (double)sum_abs4(re, im);
+                        acc += (double)sum_abs4<R>(v);
                 }
             }
             const double s = block_sum(acc, red);
+            // Every thread of the CTA is past the barriers of block_sum, so all
+            // loads of this item's tiles are complete: drop their lines from
+            // L2 without write-back (dead data; the next chunk in this slot
+            // rewrites them).  Needs whole 128-byte lines per z-block row.
+            constexpr int kLineElems = 128 / (int)sizeof(V);
+            if ((zsub_bits >= 0) && ((1 << zsub_bits) >= kLineElems) && x >= a.x_begin && x < a.x_end) {
+                const V *xb = slot_base + ((size_t)xl << lgx);
+                constexpr int lines_per_row = (1 << zsub_bits) / kLineElems;
+                constexpr int lines_per_tile = kTile / kLineElems;
+                for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
+                    const int zb = zb0 + gb;
+                    for (int L = tid; L < lines_per_tile; L += kThreads) {
+                        const int row = L / (lines_per_row > 0 ? lines_per_row : 1);
+                        const int seg = L - row * lines_per_row;
+                        discard_l2_line(xb + ((size_t)row << kTileBits) + (zb << zsub_bits) +
+                                        seg * kLineElems);
+                    }
+                }
+            }
             if (tid == 0) {
                 a.item_part[(size_t)slot * a.P2 + j] = s;
                 __threadfence();
@@ -422,30 +430,65 @@ cudaError_t query_device(DeviceInfo *info) {
                                   info->device);
 }
 
-static size_t tile_smem_bytes(int elem_bytes) { return (size_t)3 * kTile * elem_bytes; }
+static size_t tile_smem_bytes(int elem_bytes) { return (size_t)3 * kTileSlots * elem_bytes; }
 
-// Ring / chunk configuration for the two-pass kernel.  The ring of R slots of
-// C shifts (scratch R * C * elem * 2^(N - half)) is kept within ~45% of L2 so
-// the inter-pass traffic stays on chip; C > 1 reuses each pass-1 partner
-// block C times; R >= 4 keeps several chunks (and their items) in flight.
+// deterministic pseudo-random amplitudes for timing runs (values irrelevant)
+template <typename V>
+__global__ void k_fill_synthetic(V *p, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t h = (i + 1) * 0x9E3779B97F4A7C15ull;
+        h ^= h >> 31;
+        h *= 0xBF58476D1CE4E5B9ull;
+        h ^= h >> 29;
+        V v;
+        v.x = (decltype(v.x))((double)(h & 0xFFFFFF) / 16777216.0 - 0.5);
+        v.y = (decltype(v.y))((double)((h >> 24) & 0xFFFFFF) / 16777216.0 - 0.5);
+        p[i] = v;
+    }
+}
+
+cudaError_t enqueue_fill_synthetic(void *buf, int N, sre_dtype_t dtype, cudaStream_t st) {
+    const uint64_t d = 1ull << N;
+    const int grid = (int)std::min<uint64_t>((d + 255) / 256, 4096);
+    if (dtype == SRE_C128)
+        k_fill_synthetic<double2><<<grid, 256, 0, st>>>(reinterpret_cast<double2 *>(buf), d);
+    else
+        k_fill_synthetic<float2><<<grid, 256, 0, st>>>(reinterpret_cast<float2 *>(buf), d);
+    return cudaGetLastError();
+}
+
+bool large_cfg_fits(const Workspace &ws, const LargeCfg &c, int N, int half) {
+    if (c.C_log < 0 || c.C_log > 3 || c.R < 2 || c.R > kMaxRing || c.D < 1 || c.D >= c.R) return false;
+    const int h2 = N - kTileBits - half;
+    if (c.G2_log < 0 || c.G2_log > h2) return false;
+    const size_t ring = (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)ws.elem_bytes << (N - half));
+    const size_t P2 = ((size_t)1 << c.C_log) << (h2 - c.G2_log);
+    return ring <= ws.scratch_bytes && (size_t)c.R * P2 <= ws.item_part_cap;
+}
+
+// Ring / chunk configuration for the two-pass kernel.  About grid / P1
+// chunks are in pass 1 at any time (P1 = 2^h2 items per chunk), so pass 2
+// lags D = that + 1 chunks behind and the ring holds R = 2 D + 1 chunks:
+// pass-2 items then find their chunk finished and pass-1 items find their
+// slot free.  The chunk size C (shifts sharing one pass-1 partner block) is
+// the largest power of two up to 8 whose ring R * C * elem * 2^(N - half)
+// stays within 60% of L2, so the inter-pass traffic stays on chip.
 LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half) {
     LargeCfg c;
     const int h2 = N - kTileBits - half;
     const double per_x = (double)elem_bytes * (double)(1ull << (N - half));
-    const double budget = std::max(24.0 * (1 << 20), 0.45 * (double)dev.l2_bytes);
-    int C_log = 3;
-    int R = 0;
-    for (; C_log >= 0; --C_log) {
-        R = (int)(budget / (per_x * (double)(1 << C_log)));
-        if (R >= 4) break;
-    }
-    if (C_log < 0) C_log = 0;
-    c.C_log = C_log;
-    c.R = std::min(16, std::max(2, R));
-    c.D = std::max(1, c.R / 2);
-    c.G2_log = std::min(C_log, h2);
+    const double budget = std::max(24.0 * (1 << 20), 0.6 * (double)dev.l2_bytes);
     const int occ = elem_bytes == 8 ? 2 : 1;
     c.grid = std::max(1, dev.sms * occ);
+    const int P1 = 1 << h2;
+    const int inflight = (c.grid + P1 - 1) / P1;
+    c.D = std::min(inflight + 1, kMaxRing / 2 - 1);
+    c.R = 2 * c.D + 1;
+    int C_log = 3;
+    while (C_log > 0 && (double)c.R * (double)(1 << C_log) * per_x > budget) --C_log;
+    c.C_log = C_log;
+    c.G2_log = std::min(C_log, h2);
     return c;
 }
 
@@ -500,21 +543,19 @@ cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int
     SRE_TRY(cudaMalloc(&ws->status, sizeof(int)));
     SRE_TRY(cudaMalloc(&ws->result, sizeof(Result)));
     if (N_max > kTileBits) {
-        // sizes for every N up to N_max; both halves of the shift range
-        size_t scratch = 0, item_cap = 0, chunk_cap = 0;
+        // sizes for every N up to N_max and both halves of the shift range,
+        // with room for tuned configurations: chunks of a single shift, up to
+        // kMaxRing ring slots, a scratch ring of at least kTuneScratch bytes
+        size_t scratch = kTuneScratch, item_cap = 0, chunk_cap = 0;
         for (int n = kTileBits + 1; n <= N_max; ++n) {
-            size_t chunks = 0;
             for (int half = 0; half <= 1; ++half) {
                 const LargeCfg c = choose_large_cfg(dev, n, elem_bytes, half);
                 const int h2 = n - kTileBits - half;
                 scratch = std::max(scratch, (size_t)c.R * ((size_t)1 << c.C_log) *
                                                 ((size_t)elem_bytes << (n - half)));
-                const size_t P2 = ((size_t)1 << c.C_log) << (h2 - c.G2_log);
-                item_cap = std::max(item_cap, (size_t)c.R * P2);
-                const size_t span = half ? ((size_t)1 << n) - (size_t)kTile : (size_t)kTile;
-                chunks += (span >> c.C_log) + 2;
+                item_cap = std::max(item_cap, (size_t)std::max(c.R, kMaxRing) * ((size_t)8 << h2));
             }
-            chunk_cap = std::max(chunk_cap, chunks);
+            chunk_cap = std::max(chunk_cap, ((size_t)1 << n) + 4);
         }
         ws->scratch_bytes = scratch;
         ws->item_part_cap = item_cap;

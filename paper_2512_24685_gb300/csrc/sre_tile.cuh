@@ -4,7 +4,7 @@
 // The transform is the unnormalised WHT of the supplement's FWHT section:
 // stage b maps each pair (a, c) of entries whose indices differ only in bit b
 // to (a + c, a - c).  Stages commute, so the 12 bits are done in three rounds
-// of four: round k does the butterflies over bits [4k, 4k+4) entirely in
+// of four: a round does the butterflies over four index bits entirely in
 // registers; between rounds the tile is rewritten through shared memory so
 // that the next four bits become the register bits.
 //
@@ -12,10 +12,16 @@
 //   round 0: e = tid << 4 | i                          (bits 0-3 in registers)
 //   round 1: e = (tid >> 4) << 8 | i << 4 | (tid & 15)  (bits 4-7)
 //   round 2: e = i << 8 | tid                          (bits 8-11)
-// Shared memory is addressed through swz(e), which XORs index bits 4-7 and
-// 8-11 into bits 0-3.  Every round's stores and loads, the XOR-shifted
-// partner reads (e ^ x) and the strided staging of the second pass are then
-// spread over distinct banks for 8- and 16-byte elements.
+// Shared memory stores entry e at pad(e) = e + (e >> 4): one spare slot per
+// 16 entries.  Every round's stores and loads, and the XOR-shifted partner
+// reads of the single-tile kernel, then hit distinct banks for 8- and
+// 16-byte elements, and the address of slot i is the thread's base plus a
+// compile-time offset.
+//
+// FP32 complex values live in one 64-bit register pair and are combined with
+// the packed add/sub/mul/fma.rn.f32x2 instructions of sm_100+ (two IEEE
+// round-to-nearest FP32 operations per instruction: the same results as
+// scalar FP32 at half the instruction count).  FP64 values use double2.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -28,7 +34,76 @@ template <> struct V2<float> { using T = float2; };
 template <> struct V2<double> { using T = double2; };
 template <typename R> using v2_t = typename V2<R>::T;
 
-__device__ __forceinline__ int swz(int e) { return (e & ~15) | ((e ^ (e >> 4) ^ (e >> 8)) & 15); }
+constexpr int kTileSlots = 4096 + 256;  // padded shared-memory tile
+__host__ __device__ constexpr int pad(int e) { return e + (e >> 4); }
+
+// ------------------------------------------------------------ complex ops
+template <typename R> struct Cx;
+
+template <> struct Cx<float> {
+    using T = unsigned long long;  // (re, im) packed: re in the low half
+    static __device__ __forceinline__ T pack(float re, float im) {
+        T d;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(re), "f"(im));
+        return d;
+    }
+    static __device__ __forceinline__ void unpack(T v, float &re, float &im) {
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(re), "=f"(im) : "l"(v));
+    }
+    static __device__ __forceinline__ T add(T a, T b) {
+        T d;
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+        return d;
+    }
+    static __device__ __forceinline__ T sub(T a, T b) {
+        T d;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+        return d;
+    }
+    static __device__ __forceinline__ T mul(T a, T b) {
+        T d;
+        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+        return d;
+    }
+    static __device__ __forceinline__ T fma(T a, T b, T c) {
+        T d;
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+        return d;
+    }
+    static __device__ __forceinline__ T zero() { return 0ull; }
+    static __device__ __forceinline__ T from(float2 v) { return pack(v.x, v.y); }
+    static __device__ __forceinline__ float2 to(T v) {
+        float2 r;
+        unpack(v, r.x, r.y);
+        return r;
+    }
+};
+
+template <> struct Cx<double> {
+    using T = double2;
+    static __device__ __forceinline__ T pack(double re, double im) { return make_double2(re, im); }
+    static __device__ __forceinline__ void unpack(T v, double &re, double &im) {
+        re = v.x;
+        im = v.y;
+    }
+    static __device__ __forceinline__ T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ T sub(T a, T b) { return make_double2(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ T mul(T a, T b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ T fma(T a, T b, T c) {
+        return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+    }
+    static __device__ __forceinline__ T zero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ T from(double2 v) { return v; }
+    static __device__ __forceinline__ double2 to(T v) { return v; }
+};
+
+template <typename R> using cx_t = typename Cx<R>::T;
+
+// conj(b) * a for scalar factors, packed.
+template <typename R>
+__device__ __forceinline__ cx_t<R> conj_mul(R br, R bi, R ar, R ai) {
+    return Cx<R>::pack(br * ar + bi * ai, br * ai - bi * ar);
+}
 
 template <int K> __device__ __forceinline__ int elem(int tid, int i);
 template <> __device__ __forceinline__ int elem<0>(int tid, int i) { return (tid << 4) | i; }
@@ -39,7 +114,7 @@ template <> __device__ __forceinline__ int elem<2>(int tid, int i) { return (i <
 
 // Butterflies over register bits j in [0, 4) whose tile bit 4K + j < NB.
 template <int K, int NB, typename R>
-__device__ __forceinline__ void reg_stages(R (&re)[16], R (&im)[16]) {
+__device__ __forceinline__ void reg_stages(cx_t<R> (&v)[16]) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (4 * K + j < NB) {
@@ -47,45 +122,34 @@ __device__ __forceinline__ void reg_stages(R (&re)[16], R (&im)[16]) {
             for (int i = 0; i < 16; ++i) {
                 if (!(i & (1 << j))) {
                     const int p = i | (1 << j);
-                    const R ar = re[i], ai = im[i], br = re[p], bi = im[p];
-                    re[i] = ar + br;
-                    im[i] = ai + bi;
-                    re[p] = ar - br;
-                    im[p] = ai - bi;
+                    const cx_t<R> a = v[i], b = v[p];
+                    v[i] = Cx<R>::add(a, b);
+                    v[p] = Cx<R>::sub(a, b);
                 }
             }
         }
     }
 }
 
-// Move the tile from round-KA layout to round-KB layout through `buf`.
-// Moves between rounds 0 and 1 exchange register bits with thread bits 0-3,
-// i.e. data moves only inside groups of 16 threads of one warp and each warp
-// touches only its own 512-entry part of the buffer: they are ordered with
-// __syncwarp (WARP = true).  Moves between rounds 1 and 2 exchange with
-// thread bits 4-7 (across warps) and need a CTA barrier; their buffer must
-// not be the one the previous tile's cross-warp move read (callers
-// alternate two buffers).
+// Move the tile from round-KA layout to round-KB layout through `buf`
+// (kTileSlots entries).  Moves between rounds 0 and 1 exchange register bits
+// with thread bits 0-3, i.e. data moves only inside groups of 16 threads of
+// one warp and each warp touches only its own part of the buffer: they are
+// ordered with __syncwarp (WARP = true).  Moves between rounds 1 and 2
+// exchange with thread bits 4-7 (across warps) and need a CTA barrier; their
+// buffer must not be the one the previous tile's cross-warp move read
+// (callers alternate two buffers).
 template <int KA, int KB, bool WARP, typename R>
-__device__ __forceinline__ void relayout(R (&re)[16], R (&im)[16], v2_t<R> *buf, int tid) {
+__device__ __forceinline__ void relayout(cx_t<R> (&v)[16], v2_t<R> *buf, int tid) {
     if (WARP) __syncwarp();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        v2_t<R> v;
-        v.x = re[i];
-        v.y = im[i];
-        buf[swz(elem<KA>(tid, i))] = v;
-    }
+    for (int i = 0; i < 16; ++i) buf[pad(elem<KA>(tid, i))] = Cx<R>::to(v[i]);
     if (WARP)
         __syncwarp();
     else
         __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const v2_t<R> v = buf[swz(elem<KB>(tid, i))];
-        re[i] = v.x;
-        im[i] = v.y;
-    }
+    for (int i = 0; i < 16; ++i) v[i] = Cx<R>::from(buf[pad(elem<KB>(tid, i))]);
 }
 
 // Transform over tile bits [0, NB), 0 <= NB <= 12, bits 0-3 first.  Input in
@@ -94,17 +158,17 @@ __device__ __forceinline__ void relayout(R (&re)[16], R (&im)[16], v2_t<R> *buf,
 // CTA-wide round 1 -> 2 move (NB > 8): consecutive calls must alternate bufB
 // between two buffers.
 template <int NB, typename R>
-__device__ __forceinline__ void tile_fwht(R (&re)[16], R (&im)[16], v2_t<R> *bufA,
-                                          v2_t<R> *bufB, int tid) {
+__device__ __forceinline__ void tile_fwht(cx_t<R> (&v)[16], v2_t<R> *bufA, v2_t<R> *bufB,
+                                          int tid) {
     static_assert(NB >= 0 && NB <= 12, "tile transform covers 0..12 bits");
-    reg_stages<0, NB>(re, im);
+    reg_stages<0, NB, R>(v);
     if constexpr (NB > 4) {
-        relayout<0, 1, true>(re, im, bufA, tid);
-        reg_stages<1, NB>(re, im);
+        relayout<0, 1, true, R>(v, bufA, tid);
+        reg_stages<1, NB, R>(v);
     }
     if constexpr (NB > 8) {
-        relayout<1, 2, false>(re, im, bufB, tid);
-        reg_stages<2, NB>(re, im);
+        relayout<1, 2, false, R>(v, bufB, tid);
+        reg_stages<2, NB, R>(v);
     }
 }
 
@@ -113,47 +177,41 @@ __device__ __forceinline__ void tile_fwht(R (&re)[16], R (&im)[16], v2_t<R> *buf
 // contiguous), output in round-0 layout.  One CTA-wide move (bufB, to be
 // alternated between consecutive calls) and one warp-local move (bufA).
 template <typename R>
-__device__ __forceinline__ void tile_fwht12_rev(R (&re)[16], R (&im)[16], v2_t<R> *bufA,
-                                                v2_t<R> *bufB, int tid) {
-    reg_stages<2, 12>(re, im);
-    relayout<2, 1, false>(re, im, bufB, tid);
-    reg_stages<1, 12>(re, im);
-    relayout<1, 0, true>(re, im, bufA, tid);
-    reg_stages<0, 12>(re, im);
-}
-
-template <int NB> struct FinalRound { static constexpr int value = (NB - 1) / 4; };
-
-// sum_i (Re F_i)^4 + (Im F_i)^4 over the thread's 16 entries, in R.
-template <typename R>
-__device__ __forceinline__ R sum_re4_im4(const R (&re)[16], const R (&im)[16]) {
-    R s = R(0);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const R a = re[i] * re[i], b = im[i] * im[i];
-        s += a * a + b * b;
-    }
-    return s;
+__device__ __forceinline__ void tile_fwht12_rev(cx_t<R> (&v)[16], v2_t<R> *bufA, v2_t<R> *bufB,
+                                                int tid) {
+    reg_stages<2, 12, R>(v);
+    relayout<2, 1, false, R>(v, bufB, tid);
+    reg_stages<1, 12, R>(v);
+    relayout<1, 0, true, R>(v, bufA, tid);
+    reg_stages<0, 12, R>(v);
 }
 
 // sum_i |F_i|^4 over the thread's 16 entries, in R.
 template <typename R>
-__device__ __forceinline__ R sum_abs4(const R (&re)[16], const R (&im)[16]) {
+__device__ __forceinline__ R sum_abs4(const cx_t<R> (&v)[16]) {
     R s = R(0);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const R m = re[i] * re[i] + im[i] * im[i];
+        R re, im;
+        Cx<R>::unpack(Cx<R>::mul(v[i], v[i]), re, im);
+        const R m = re + im;
         s += m * m;
     }
     return s;
 }
 
-// Load one complex amplitude of input type In (float2 / double2) as R.
-template <typename R, typename In>
-__device__ __forceinline__ void load_amp(const In *p, uint64_t idx, R &re, R &im) {
-    const In v = __ldg(p + idx);
-    re = (R)v.x;
-    im = (R)v.y;
+// sum_i (Re F_i)^4 + (Im F_i)^4 over the thread's 16 entries, in R.
+template <typename R>
+__device__ __forceinline__ R sum_re4_im4(const cx_t<R> (&v)[16]) {
+    cx_t<R> acc = Cx<R>::zero();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const cx_t<R> sq = Cx<R>::mul(v[i], v[i]);
+        acc = Cx<R>::fma(sq, sq, acc);
+    }
+    R a, b;
+    Cx<R>::unpack(acc, a, b);
+    return a + b;
 }
 
 // Deterministic block-wide FP64 sum (fixed tree); result valid in thread 0.
@@ -175,6 +233,12 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Drop a 128-byte L2 line without writing it back (its contents become
+// undefined).  Used on inter-pass scratch once every reader is done with it.
+__device__ __forceinline__ void discard_l2_line(const void *p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

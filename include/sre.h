@@ -116,7 +116,9 @@ SRE_API sre_status_t sre_plan_get_mode(sre_plan_t plan, sre_mode_t *mode);
  * the remaining bits).  x_batch_log: log2 of the shifts that share one
  * pass-1 partner block (0..3); ring_slots: chunks held in the ring (>= 2);
  * lag: how many chunks pass 2 trails pass 1 (1 <= lag < ring_slots);
- * pass2_tiles_log: log2 of the 2^12-entry tiles per pass-2 work item.
+ * pass2_tiles_log: log2 of the 2^12-entry tiles per pass-2 work item;
+ * pass1_blocks_log: log2 of the consecutive 2^12-entry blocks of t per
+ * pass-1 work item.
  * A value of -1 keeps the library's choice for that field; all -1 restores
  * the defaults.  The scratch ring must fit the plan's allocation
  * (SRE_EINVAL otherwise).  Applies to the halved shifts (x >= 4096).
@@ -126,6 +128,7 @@ typedef struct {
     int ring_slots;
     int lag;
     int pass2_tiles_log;
+    int pass1_blocks_log;
 } sre_tuning_t;
 SRE_API sre_status_t sre_plan_set_tuning(sre_plan_t plan, const sre_tuning_t *tuning);
 SRE_API sre_status_t sre_plan_get_tuning(sre_plan_t plan, int N, sre_tuning_t *tuning);

@@ -45,10 +45,11 @@ struct sre_plan_s {
     sre::BatchedContext *batched = nullptr;
     bool profiling = false;
     unsigned long long extra_launches = 0;  // launches of workspaces that were freed
-    sre_tuning_t user = {-1, -1, -1, -1};           // sre_plan_set_tuning
+    sre_tuning_t user = {-1, -1, -1, -1, -1};           // sre_plan_set_tuning
     sre::LargeCfg tuned[SRE_MAX_QUBITS + 1];        // sre_plan_autotune results
     bool has_tuned[SRE_MAX_QUBITS + 1] = {};
     void *tune_state = nullptr;                     // synthetic state for autotuning
+    sre::LargeCfg batch_cfg[SRE_MAX_QUBITS + 1];    // configurations handed to batches
 };
 
 namespace {
@@ -216,7 +217,9 @@ static sre::LargeCfg plan_cfg(sre_plan_t p, int N) {
     if (p->user.ring_slots >= 0) c.R = p->user.ring_slots;
     if (p->user.lag >= 0) c.D = p->user.lag;
     if (p->user.pass2_tiles_log >= 0) c.G2_log = p->user.pass2_tiles_log;
+    if (p->user.pass1_blocks_log >= 0) c.B1_log = p->user.pass1_blocks_log;
     c.G2_log = std::min(c.G2_log, N - sre::kTileBits - 1);
+    c.B1_log = std::min(c.B1_log, N - sre::kTileBits - 1);
     return c;
 }
 
@@ -252,7 +255,7 @@ static sre_status_t enqueue_plan_cfg(sre_plan_t p, const void *d_state, int N, u
 sre_status_t sre_plan_set_tuning(sre_plan_t p, const sre_tuning_t *t) {
     if (!p || !t) return SRE_EINVAL;
     if (t->x_batch_log > 3 || t->ring_slots > sre::kMaxRing || (t->ring_slots >= 0 && t->ring_slots < 2) ||
-        (t->lag >= 0 && t->lag < 1) || t->pass2_tiles_log > 12)
+        (t->lag >= 0 && t->lag < 1) || t->pass2_tiles_log > 12 || t->pass1_blocks_log > 12)
         return SRE_EINVAL;
     p->user = *t;
     return SRE_OK;
@@ -261,7 +264,7 @@ sre_status_t sre_plan_set_tuning(sre_plan_t p, const sre_tuning_t *t) {
 sre_status_t sre_plan_get_tuning(sre_plan_t p, int N, sre_tuning_t *t) {
     if (!p || !t || N < 1 || N > p->N) return SRE_EINVAL;
     if (N <= sre::kTileBits) {
-        *t = {-1, -1, -1, -1};
+        *t = {-1, -1, -1, -1, -1};
         return SRE_OK;
     }
     const sre::LargeCfg c = plan_cfg(p, N);
@@ -269,6 +272,7 @@ sre_status_t sre_plan_get_tuning(sre_plan_t p, int N, sre_tuning_t *t) {
     t->ring_slots = c.R;
     t->lag = c.D;
     t->pass2_tiles_log = c.G2_log;
+    t->pass1_blocks_log = c.B1_log;
     return SRE_OK;
 }
 
@@ -291,15 +295,20 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
     std::vector<sre::LargeCfg> cands;
     for (int C_log = 0; C_log <= 3; ++C_log)
         for (int dm = 1; dm <= 2; ++dm)
-            for (int g = 0; g <= 1; ++g) {
+            for (int g = 0; g <= 2; ++g) {
                 sre::LargeCfg c = base;
                 c.C_log = C_log;
-                c.D = std::min(dm * inflight + 1, sre::kMaxRing / 2 - 1);
+                // bigger items when few shifts share a partner block
+                c.B1_log = std::min(h2, std::max(0, (g == 2 ? 3 : 2) - C_log));
+                const int items1 = 1 << (h2 - c.B1_log);
+                const int infl = std::max(1, (base.grid + items1 - 1) / items1);
+                c.D = std::min(dm * infl + 1, sre::kMaxRing / 2 - 1);
                 c.R = 2 * c.D + 1;
-                c.G2_log = g ? std::min(C_log, h2) : 0;
-                if (g == 0 && std::min(C_log, h2) == 0) continue;  // same as g = 1
+                c.G2_log = std::min(h2, g == 0 ? C_log : C_log + g);
+                if (g == 0) c.B1_log = 0;
                 if (sre::large_cfg_fits(p->ws, c, N, 1)) cands.push_back(c);
             }
+    (void)inflight;
     if (cands.empty()) return SRE_OK;
     // a slice of halved shifts worth ~2^34 entries of work
     const uint64_t d = 1ull << N;
@@ -345,6 +354,7 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
         best->ring_slots = best_c.R;
         best->lag = best_c.D;
         best->pass2_tiles_log = best_c.G2_log;
+        best->pass1_blocks_log = best_c.B1_log;
     }
     if (ms_out) *ms_out = best_ms;
     return SRE_OK;
@@ -416,7 +426,8 @@ sre_status_t sre_sum4_range(sre_plan_t p, const void *d_state, int N, uint64_t x
 
 sre_status_t sre_m2_batched(sre_plan_t p, const void *const *d_states, const int *Ns, int count,
                             sre_stream_t stream, double *d_m2_out) {
-    if (!p || !d_states || !Ns || !d_m2_out || count < 1) return SRE_EINVAL;
+    if (!p || !d_states || !Ns || !d_m2_out || count < 1 || count > 65535) return SRE_EINVAL;
+    if (((uintptr_t)d_m2_out) % 8) return SRE_EALIGN;
     for (int i = 0; i < count; ++i) {
         sre_status_t s = check_state(p, d_states[i], Ns[i]);
         if (s != SRE_OK) return s;
@@ -425,8 +436,16 @@ sre_status_t sre_m2_batched(sre_plan_t p, const void *const *d_states, const int
         p->batched = sre::batched_create(p->dev);
         if (!p->batched) return SRE_ENOMEM;
     }
+    const sre::LargeCfg *tuned[SRE_MAX_QUBITS + 1];
+    for (int n = 0; n <= SRE_MAX_QUBITS; ++n) {
+        tuned[n] = nullptr;
+        if (n > sre::kTileBits && n <= p->N) {
+            p->batch_cfg[n] = plan_cfg(p, n);
+            tuned[n] = &p->batch_cfg[n];
+        }
+    }
     cudaError_t e = sre::batched_run(p->batched, p->ws, p->dev, d_states, Ns, count, p->dtype,
-                                     p->mode, (cudaStream_t)stream, d_m2_out, p->wait_ns);
+                                     p->mode, (cudaStream_t)stream, d_m2_out, p->wait_ns, tuned);
     return e == cudaSuccess ? SRE_OK : cuda_fail(e);
 }
 

@@ -13,9 +13,12 @@ BatchedContext *batched_create(const DeviceInfo &dev);
 void batched_destroy(BatchedContext *ctx);
 
 // M2 of `count` states (device pointers, uneven N) into d_m2_out[count].
+// tuned_half[N] (may be null, or hold nulls) gives autotuned two-pass
+// configurations of the halved shifts per N.
 cudaError_t batched_run(BatchedContext *ctx, const Workspace &ws, const DeviceInfo &dev,
                         const void *const *d_states, const int *Ns, int count, sre_dtype_t dtype,
-                        sre_mode_t mode, cudaStream_t stream, double *d_m2_out, long long wait_ns);
+                        sre_mode_t mode, cudaStream_t stream, double *d_m2_out, long long wait_ns,
+                        const LargeCfg *const *tuned_half);
 
 // Tensor-core split-precision modes (BF16 / FP16 / TF32 hi-lo Hadamard stages).
 bool tc_mode_available(sre_mode_t mode);

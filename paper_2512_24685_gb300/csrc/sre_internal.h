@@ -35,6 +35,7 @@ struct LargeCfg {
     int R;       // ring slots of inter-pass scratch
     int D;       // lag (in chunks) of pass 2 behind pass 1, D < R
     int G2_log;  // log2 tiles per pass-2 work item
+    int B1_log;  // log2 consecutive blocks per pass-1 work item
     int grid;    // persistent CTAs
 };
 
@@ -99,6 +100,31 @@ cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d
                        sre_dtype_t dtype, int N, uint64_t x_begin, uint64_t x_end,
                        sre_mode_t mode, cudaStream_t stream, double *d_m2, double *d_per_x,
                        long long wait_ns, LargeCfg *cfg_override);
+
+// ---- batched evaluation: states grouped in classes of equal N.
+struct BatchClass {
+    int N = 0, S = 0;         // size and number of states of the class
+    int small_grid = 0;       // N <= 12: CTAs of the single-tile launch
+    LargeCfg cfg_full{}, cfg_half{};  // N > 12: shifts < 4096 / halved shifts
+    long long cps_full = 0, cps_half = 0;  // chunks per state of each part
+    size_t parts_off = 0, parts_n = 0;     // partials of the class
+    size_t chunks_max = 0;                 // counters needed by one launch
+};
+
+BatchClass batch_class_layout(const DeviceInfo &dev, const Workspace &ws, int N, int S,
+                              sre_mode_t mode, const LargeCfg *tuned_half);
+cudaError_t enqueue_batch_class(const Workspace &ws, const DeviceInfo &dev, const BatchClass &L,
+                                const void *const *d_ptrs, double *parts, unsigned *counters,
+                                size_t chunk_cap, sre_mode_t mode, cudaStream_t st,
+                                long long wait_ns);
+cudaError_t enqueue_batch_norm(const Workspace &ws, const void *const *d_ptrs, const int *d_Ns,
+                               int count, double *npart, int *flags, sre_mode_t mode,
+                               cudaStream_t st);
+cudaError_t enqueue_batch_finalize(const Workspace &ws, const void *seg, const double *parts,
+                                   const double *npart, const int *flags, const int *d_Ns,
+                                   const int *d_out_index, int count, double *m2_out,
+                                   cudaStream_t st);
+cudaError_t enqueue_convert(const void *src, sre_dtype_t from, void *dst, int N, cudaStream_t st);
 
 // Copy the result block to d_out2 = {S, n2} (for the range API).
 cudaError_t enqueue_copy_sums(const Workspace &ws, double *d_out2, cudaStream_t stream);

@@ -75,9 +75,15 @@ __global__ void __launch_bounds__(kThreads) k_norm(const v2_t<R> *__restrict__ p
 // over the low NB = N bits of the tile index.
 template <typename R, int NB>
 __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ psi,
+                                                    const void *const *__restrict__ psis,
+                                                    long long tiles_per_state,
                                                     uint64_t x_begin, uint64_t x_end,
                                                     long long ntiles,
                                                     double *__restrict__ part) {
+    // Single state: psis == nullptr.  Several states of the same N: psis[s] is
+    // state s and tiles are numbered state-major.  Tile g's sum goes to
+    // part[g] (fixed-order tree inside the tile), so a state's partials do not
+    // depend on the grid or on the other states of a batch.
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = v2_t<R>;
     V *psi_s = reinterpret_cast<V *>(smem_raw);
@@ -87,15 +93,22 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
     constexpr int N = NB;
     constexpr int d = 1 << N;
     const int tid = threadIdx.x;
-    for (int t = tid; t < d; t += kThreads) psi_s[pad(t)] = psi[t];
-    __syncthreads();
 
-    double acc = 0.0;
+    long long cur = -1;
     for (long long g = blockIdx.x; g < ntiles; g += gridDim.x) {
+        const long long sidx = psis ? g / tiles_per_state : 0;
+        const long long gl = g - sidx * tiles_per_state;
+        if (sidx != cur) {
+            const V *src = psis ? reinterpret_cast<const V *>(psis[sidx]) : psi;
+            __syncthreads();
+            for (int t = tid; t < d; t += kThreads) psi_s[pad(t)] = src[t];
+            __syncthreads();
+            cur = sidx;
+        }
         cx_t<R> v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const uint64_t flat = ((uint64_t)g << kTileBits) | (uint64_t)elem<0>(tid, i);
+            const uint64_t flat = ((uint64_t)gl << kTileBits) | (uint64_t)elem<0>(tid, i);
             const uint64_t x = x_begin + (flat >> N);
             const int t = (int)(flat & (d - 1));
             if (x < x_end) {
@@ -107,11 +120,10 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
             }
         }
         tile_fwht<NB, R>(v, bufA, bufB, tid);
-        acc += (double)sum_abs4<R>(v);
-        __syncthreads();  // bufB is reused by the next tile
+        // block_sum's barriers also protect bufB before the next tile
+        const double s = block_sum((double)sum_abs4<R>(v), red);
+        if (tid == 0) part[g] = s;
     }
-    const double s = block_sum(acc, red);
-    if (tid == 0) part[blockIdx.x] = s;
 }
 
 // -------------------------------------------------------- N > 12: k_large
@@ -121,9 +133,10 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
 // Shifts are grouped in chunks of C = 2^C_log consecutive values (aligned, so
 // a chunk shares x_h = x >> 12 and, for halved chunks, the pivot bit).  A
 // chunk owns one slot of a ring of R scratch slots.  Its work items:
-//   pass 1, P1 = 2^h2 items: block t'_h of every shift of the chunk -- the
-//           XOR-shifted products of one 2^12 block of t, the 12 low transform
-//           bits, written to scratch[slot][shift][t'_h][z_l];
+//   pass 1, P1 = 2^(h2 - B1_log) items of 2^B1_log consecutive blocks t'_h,
+//           each for every shift of the chunk -- the XOR-shifted products of
+//           one 2^12 block of t, the 12 low transform bits, written to
+//           scratch[slot][shift][t'_h][z_l];
 //   pass 2, P2 items of 2^G2_log tiles: for one shift and a range of z-blocks,
 //           the 2^h2 blocks t'_h of each z-block are read back, the h2 high
 //           bits are transformed and |A|^4 is reduced.
@@ -140,12 +153,14 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
 // j >= 12, the restriction removes one high bit: block t'_h maps to
 // t_h = t'_h with a zero inserted at bit j - 12, and h2 = N - 13.
 struct LargeArgs {
-    const void *psi;
+    const void *psi;           // the state (single-state launch)
+    const void *const *psis;   // or: states of one batch class (device array)
+    long long chunks_per_state;  // chunks of each state (batch class)
     int N, h2;                 // h2: pass-2 transform bits (N - 12, or N - 13 halved)
     int half;
     uint64_t x_begin, x_end;   // evaluated shift range
     uint64_t x0;               // x_begin rounded down to a chunk boundary
-    int C_log, R, D, G2_log;
+    int C_log, R, D, G2_log, B1_log;
     long long n_chunks;
     int P1, P2;                // items per chunk in pass 1 / pass 2
     long long n_items;
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
     const int tid = threadIdx.x;
     const int lgx = a.N - (HALF ? 1 : 0);        // log2 scratch entries per shift
     const int C = 1 << a.C_log;
-    const V *psi = reinterpret_cast<const V *>(a.psi);
+    const V *psi0 = reinterpret_cast<const V *>(a.psi);
     V *scratch = reinterpret_cast<V *>(a.scratch);
     constexpr int zsub_bits = kTileBits - H2;     // z entries per block in pass 2
     const int ipx_log = H2 - a.G2_log;            // pass-2 items per shift (log2)
@@ -237,17 +252,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
         bool pass1;
         decode_item(a, item, c, r, pass1);
         const int slot = (int)(c % a.R);
-        const uint64_t xc = a.x0 + ((uint64_t)c << a.C_log);
+        // batch class: chunk c belongs to state c / chunks_per_state
+        long long cl = c;
+        const V *psi = psi0;
+        if (a.psis) {
+            const long long sidx = c / a.chunks_per_state;
+            cl = c - sidx * a.chunks_per_state;
+            psi = reinterpret_cast<const V *>(a.psis[sidx]);
+        }
+        const uint64_t xc = a.x0 + ((uint64_t)cl << a.C_log);
         V *slot_base = scratch + (size_t)slot * ((size_t)C << lgx);
 
         if (pass1) {
-            // ---------------- pass 1: block t'_h = r of every shift in the chunk
-            const int tp = r;
-            int th = tp;
-            if (HALF) {
-                const int jh = (63 - __clzll((long long)xc)) - kTileBits;
-                th = ((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1));
-            }
+            // ---------------- pass 1: blocks t'_h in [r 2^B1, (r+1) 2^B1) of
+            // every shift in the chunk
             if (tid == 0) {
                 s_flag = 1;
                 if (c >= a.R) s_flag = wait_counter(a.freed + (c - a.R), 1u, a.status, a.wait_ns);
@@ -256,42 +274,47 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
             if (!s_flag) break;
             const uint64_t xh = xc >> kTileBits;
             const int xl0 = (int)(xc & (kTile - 1));
-            // Round-2 layout: thread tid holds t_l = i << 8 | tid of block th
-            // (own factors phi_t in registers); its partners t ^ x are
-            // t_l ^ xlow of block th ^ x_h, read coalesced (each warp load
-            // covers one aligned 256-entry run).
-            R ar[16], ai[16];
-            {
-                const V *pa = psi + ((uint64_t)th << kTileBits) + tid;
+            const int jh = HALF ? (63 - __clzll((long long)xc)) - kTileBits : 0;
+            for (int kb = 0; kb < (1 << a.B1_log); ++kb) {
+                const int tp = (r << a.B1_log) + kb;
+                const int th = HALF ? (((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1))) : tp;
+                // Round-2 layout: thread tid holds t_l = i << 8 | tid of block th
+                // (own factors phi_t in registers); its partners t ^ x are
+                // t_l ^ xlow of block th ^ x_h, read coalesced (each warp load
+                // covers one aligned 256-entry run).
+                R ar[16], ai[16];
+                {
+                    const V *pa = psi + ((uint64_t)th << kTileBits) + tid;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const V va = __ldg(pa + (i << 8));
-                    ar[i] = va.x;
-                    ai[i] = va.y;
+                    for (int i = 0; i < 16; ++i) {
+                        const V va = __ldg(pa + (i << 8));
+                        ar[i] = va.x;
+                        ai[i] = va.y;
+                    }
                 }
-            }
-            const V *pb = psi + (((uint64_t)th ^ xh) << kTileBits);
-            for (int xl = 0; xl < C; ++xl) {
-                const uint64_t x = xc + (uint64_t)xl;
-                if (x < a.x_begin || x >= a.x_end) continue;
-                const int xlow = xl0 + xl;
-                const V *pbx = pb + (tid ^ (xlow & 255));
-                const int q = xlow >> 8;
-                cx_t<R> v[16];
+                const V *pb = psi + (((uint64_t)th ^ xh) << kTileBits);
+                for (int xl = 0; xl < C; ++xl) {
+                    const uint64_t x = xc + (uint64_t)xl;
+                    if (x < a.x_begin || x >= a.x_end) continue;
+                    const int xlow = xl0 + xl;
+                    const V *pbx = pb + (tid ^ (xlow & 255));
+                    const int q = xlow >> 8;
+                    cx_t<R> v[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const V b = __ldg(pbx + ((i ^ q) << 8));
-                    v[i] = conj_mul<R>(b.x, b.y, ar[i], ai[i]);  // conj(phi_{t^x}) * phi_t
+                    for (int i = 0; i < 16; ++i) {
+                        const V b = __ldg(pbx + ((i ^ q) << 8));
+                        v[i] = conj_mul<R>(b.x, b.y, ar[i], ai[i]);  // conj(phi_{t^x}) * phi_t
+                    }
+                    V *bB = (tcount & 1) ? bufC : bufB;
+                    ++tcount;
+                    tile_fwht12_rev<R>(v, bufA, bB, tid);
+                    // output in round-0 layout (z_l = 16 tid + i) stored at the
+                    // bit-permuted position i << 8 | tid: coalesced stores; pass 2
+                    // only sums over z, so the order of z inside a block is free
+                    V *o = slot_base + ((size_t)xl << lgx) + ((size_t)tp << kTileBits) + tid;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) __stcg(o + (i << 8), Cx<R>::to(v[i]));
                 }
-                V *bB = (tcount & 1) ? bufC : bufB;
-                ++tcount;
-                tile_fwht12_rev<R>(v, bufA, bB, tid);
-                // output in round-0 layout (z_l = 16 tid + i) stored at the
-                // bit-permuted position i << 8 | tid: coalesced stores; pass 2
-                // only sums over z, so the order of z inside a block is free
-                V *o = slot_base + ((size_t)xl << lgx) + ((size_t)tp << kTileBits) + tid;
-#pragma unroll
-                for (int i = 0; i < 16; ++i) __stcg(o + (i << 8), Cx<R>::to(v[i]));
             }
             __syncthreads();
             if (tid == 0) {
@@ -384,26 +407,39 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
 
 // ------------------------------------------------------------- finalize
 
-__global__ void __launch_bounds__(kFinalThreads) k_finalize(const double *__restrict__ parts,
-                                                            long long nparts,
-                                                            const double *__restrict__ npart,
-                                                            int nn, int N, const int *flags,
-                                                            const int *status, Result *res,
-                                                            double *d_m2) {
-    __shared__ double red[kFinalThreads / 32];
+// Fixed-order FP64 sum of two segments of partials by one warp: lane l adds
+// entries l, l+32, ... of each segment in order, then a fixed shuffle tree.
+// Shared by the single-state and the batch finalize, so a state's M2 is
+// bitwise the same in either.
+__device__ __forceinline__ double warp_sum_segments(const double *p, long long o1, long long n1,
+                                                    long long o2, long long n2) {
+    const int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (long long k = threadIdx.x; k < nparts; k += blockDim.x) s += parts[k];
-    const double S = block_sum(s, red);
-    double n = 0.0;
-    for (int k = threadIdx.x; k < nn; k += blockDim.x) n += npart[k];
-    const double n2 = block_sum(n, red);
+    for (long long k = lane; k < n1; k += 32) s += p[o1 + k];
+    for (long long k = lane; k < n2; k += 32) s += p[o2 + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;  // valid in lane 0
+}
+
+__device__ __forceinline__ double m2_from(double S, double n2, int N, bool bad) {
+    // M2 = -log2(S / (d n2^4)), in logs so tiny norms do not underflow
+    return bad ? __longlong_as_double(0x7ff8000000000000ll)
+               : -(log2(S) - (double)N - 4.0 * log2(n2));
+}
+
+// One warp: S from the partial segments [o1, o1+n1) and [o2, o2+n2), n2 from
+// the norm partials, M2 and the status.
+__global__ void k_finalize(const double *__restrict__ parts, long long o1, long long n1, long long o2,
+                           long long n2c, const double *__restrict__ npart, int nn, int N,
+                           const int *flags, const int *status, Result *res, double *d_m2) {
+    const double S = warp_sum_segments(parts, o1, n1, o2, n2c);
+    const double n2 = warp_sum_segments(npart, 0, nn, 0, 0);
     if (threadIdx.x == 0) {
         int st = *status;
         if (st == 0 && (*flags & kFlagNonFinite)) st = SRE_ENONFINITE;
         if (st == 0 && !(n2 > 0.0)) st = SRE_EZERO;
-        // M2 = -log2(S / (d n2^4)), written in logs so tiny norms do not underflow
-        const double m2 = st ? __longlong_as_double(0x7ff8000000000000ll)
-                             : -(log2(S) - (double)N - 4.0 * log2(n2));
+        const double m2 = m2_from(S, n2, N, st != 0);
         res->m2 = m2;
         res->S = S;
         res->n2 = n2;
@@ -461,7 +497,7 @@ cudaError_t enqueue_fill_synthetic(void *buf, int N, sre_dtype_t dtype, cudaStre
 bool large_cfg_fits(const Workspace &ws, const LargeCfg &c, int N, int half) {
     if (c.C_log < 0 || c.C_log > 3 || c.R < 2 || c.R > kMaxRing || c.D < 1 || c.D >= c.R) return false;
     const int h2 = N - kTileBits - half;
-    if (c.G2_log < 0 || c.G2_log > h2) return false;
+    if (c.G2_log < 0 || c.G2_log > h2 || c.B1_log < 0 || c.B1_log > h2) return false;
     const size_t ring = (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)ws.elem_bytes << (N - half));
     const size_t P2 = ((size_t)1 << c.C_log) << (h2 - c.G2_log);
     return ring <= ws.scratch_bytes && (size_t)c.R * P2 <= ws.item_part_cap;
@@ -489,6 +525,7 @@ LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half
     while (C_log > 0 && (double)c.R * (double)(1 << C_log) * per_x > budget) --C_log;
     c.C_log = C_log;
     c.G2_log = std::min(C_log, h2);
+    c.B1_log = 0;
     return c;
 }
 
@@ -537,7 +574,7 @@ cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int
     } while (0)
     SRE_TRY(cudaMalloc(&ws->npart, sizeof(double) * kNormBlocks));
     SRE_TRY(cudaMalloc(&ws->flags, sizeof(int)));
-    ws->part_cap = std::max(1, dev.sms * 4);
+    ws->part_cap = kTile;  // one partial per tile of an N <= 12 state
     SRE_TRY(cudaMalloc(&ws->part, sizeof(double) * ws->part_cap));
     SRE_TRY(cudaMalloc(&ws->work, sizeof(unsigned long long) * 2));
     SRE_TRY(cudaMalloc(&ws->status, sizeof(int)));
@@ -570,30 +607,36 @@ cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int
 }
 
 template <typename R, int NB>
-static cudaError_t launch_small_nb(const void *psi, uint64_t x_begin, uint64_t x_end,
-                                   const Workspace &ws, const DeviceInfo &dev, cudaStream_t st,
-                                   int *nparts) {
+static cudaError_t launch_small_nb(const void *psi, const void *const *psis, int nstates,
+                                   uint64_t x_begin, uint64_t x_end, double *part, int part_cap,
+                                   const DeviceInfo &dev, cudaStream_t st, int *nparts,
+                                   int forced_grid = 0) {
     const size_t smem = tile_smem_bytes(sizeof(v2_t<R>));
     auto kern = k_small<R, NB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint64_t flat = (x_end - x_begin) << NB;
-    const long long ntiles = (long long)((flat + kTile - 1) >> kTileBits);
+    const long long tps = (long long)((flat + kTile - 1) >> kTileBits);
+    const long long ntiles = tps * nstates;
+    if (ntiles > part_cap) return cudaErrorInvalidValue;
     const int occ = sizeof(R) == 4 ? 2 : 1;
-    const int grid = (int)std::min<long long>(ntiles, std::min(ws.part_cap, dev.sms * occ));
-    kern<<<grid, kThreads, smem, st>>>(reinterpret_cast<const v2_t<R> *>(psi), x_begin, x_end,
-                                       ntiles, ws.part);
-    *nparts = grid;
+    const int grid = forced_grid > 0 ? forced_grid
+                                     : (int)std::min<long long>(ntiles, (long long)dev.sms * occ);
+    if (grid < 1) return cudaErrorInvalidValue;
+    kern<<<grid, kThreads, smem, st>>>(reinterpret_cast<const v2_t<R> *>(psi), psis, tps, x_begin,
+                                       x_end, ntiles, part);
+    *nparts = (int)ntiles;
     return cudaGetLastError();
 }
 
 template <typename R>
-static cudaError_t launch_small(int N, const void *psi, uint64_t xb, uint64_t xe,
-                                const Workspace &ws, const DeviceInfo &dev, cudaStream_t st,
-                                int *nparts) {
+static cudaError_t launch_small(int N, const void *psi, const void *const *psis, int nstates,
+                                uint64_t xb, uint64_t xe, double *part, int part_cap,
+                                const DeviceInfo &dev, cudaStream_t st, int *nparts,
+                                int forced_grid = 0) {
     switch (N) {
 #define SRE_CASE(n) \
-    case n: return launch_small_nb<R, n>(psi, xb, xe, ws, dev, st, nparts);
+    case n: return launch_small_nb<R, n>(psi, psis, nstates, xb, xe, part, part_cap, dev, st, nparts, forced_grid);
         SRE_CASE(1) SRE_CASE(2) SRE_CASE(3) SRE_CASE(4) SRE_CASE(5) SRE_CASE(6)
         SRE_CASE(7) SRE_CASE(8) SRE_CASE(9) SRE_CASE(10) SRE_CASE(11) SRE_CASE(12)
 #undef SRE_CASE
@@ -631,6 +674,8 @@ static cudaError_t make_large_args(LargeArgs *a, const Workspace &ws, const Devi
     const LargeCfg c = ovr ? *ovr : choose_large_cfg(dev, N, elem_bytes, half);
     LargeArgs &A = *a;
     A.psi = psi;
+    A.psis = nullptr;
+    A.chunks_per_state = 0;
     A.N = N;
     A.half = half;
     A.h2 = N - kTileBits - half;
@@ -643,7 +688,8 @@ static cudaError_t make_large_args(LargeArgs *a, const Workspace &ws, const Devi
     A.n_chunks = (long long)((xe - A.x0 + (1ull << c.C_log) - 1) >> c.C_log);
     A.D = (int)std::max<long long>(1, std::min<long long>(std::min(c.D, c.R - 1), A.n_chunks));
     if (A.R < 2) return cudaErrorInvalidValue;
-    A.P1 = 1 << A.h2;
+    A.B1_log = std::max(0, std::min(c.B1_log, A.h2));
+    A.P1 = 1 << (A.h2 - A.B1_log);
     A.P2 = (1 << c.C_log) << (A.h2 - A.G2_log);
     A.n_items = A.n_chunks * (long long)(A.P1 + A.P2);
     const size_t need_scratch = (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)elem_bytes << (N - half));
@@ -682,16 +728,19 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ws.launches += 2;  // k_norm + k_finalize
     const double *parts = nullptr;
-    long long nparts = 0;
+    long long nparts = 0, seg1 = 0;  // large path: [0, seg1) full shifts, [seg1, nparts) halved
     if (N <= kTileBits) {
         int np = 0;
         if (ws.ev_begin && (e = cudaEventRecord(ws.ev_begin, st)) != cudaSuccess) return e;
-        if ((e = launch_small<R>(N, psi, x_begin, x_end, ws, dev, st, &np)) != cudaSuccess) return e;
+        if ((e = launch_small<R>(N, psi, nullptr, 1, x_begin, x_end, ws.part, ws.part_cap, dev, st,
+                                 &np)) != cudaSuccess)
+            return e;
         if (ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
         ws.main_kernel = "k_small";
         ws.launches += 1;
         parts = ws.part;
         nparts = np;
+        seg1 = np;
     } else {
         // shifts below 4096 (pivot bit inside the 12-bit block): full
         // transform; shifts from 4096 up: conjugate-symmetry halving
@@ -719,14 +768,15 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
             if (e != cudaSuccess) return e;
             ws.launches += 1;
             chunks += (size_t)a.n_chunks;
+            if (!half) seg1 = (long long)chunks;
         }
         if (ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
         ws.main_kernel = "k_large";
         parts = ws.chunk_sum;
         nparts = (long long)chunks;
     }
-    k_finalize<<<1, kFinalThreads, 0, st>>>(parts, nparts, ws.npart, kNormBlocks, N, ws.flags,
-                                            ws.status, ws.result, d_m2);
+    k_finalize<<<1, 32, 0, st>>>(parts, 0, seg1, seg1, nparts - seg1, ws.npart, kNormBlocks, N,
+                                 ws.flags, ws.status, ws.result, d_m2);
     return cudaGetLastError();
 }
 
@@ -758,6 +808,193 @@ cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d
                                     cfg_override);
     return enqueue_m2_t<float>(ws, dev, psi, N, x_begin, x_end, stream, d_m2, d_per_x, wait_ns,
                                cfg_override);
+}
+
+// ------------------------------------------------------------------ batch
+
+// n2 of several states (state s = blockIdx.y, its size from Ns[s]);
+// partials in npart[s * kNormBlocks + b], flags[s] |= non-finite.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_norm_batch(const void *const *__restrict__ psis,
+                                                         const int *__restrict__ Ns,
+                                                         double *__restrict__ npart,
+                                                         int *__restrict__ flags) {
+    __shared__ double red[kThreads / 32];
+    const int sidx = blockIdx.y;
+    const v2_t<R> *psi = reinterpret_cast<const v2_t<R> *>(psis[sidx]);
+    const uint64_t d = 1ull << Ns[sidx];
+    double s = 0.0;
+    int bad = 0;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < d;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const v2_t<R> v = psi[t];
+        const double re = (double)v.x, im = (double)v.y;
+        if (!isfinite(re) || !isfinite(im)) bad = 1;
+        s += re * re + im * im;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags + sidx, kFlagNonFinite);
+    const double b = block_sum(s, red);
+    if (threadIdx.x == 0) npart[(size_t)sidx * gridDim.x + blockIdx.x] = b;
+}
+
+// M2 of every state of a batch: one warp per state, the same fixed-order
+// segment sums as the single-state finalize (seg = {off1, n1, off2, n2}).
+__global__ void k_finalize_batch(const longlong4 *__restrict__ seg, const double *__restrict__ parts,
+                                 const double *__restrict__ npart, int nnorm,
+                                 const int *__restrict__ flags, const int *__restrict__ Ns,
+                                 const int *__restrict__ out_index, int count, const int *status,
+                                 double *__restrict__ m2_out) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= count) return;
+    const longlong4 g = seg[w];
+    const double S = warp_sum_segments(parts, g.x, g.y, g.z, g.w);
+    const double n = warp_sum_segments(npart, (long long)w * nnorm, nnorm, 0, 0);
+    if ((threadIdx.x & 31) == 0) {
+        const bool bad = (*status != 0) || (flags[w] & kFlagNonFinite) || !(n > 0.0);
+        m2_out[out_index[w]] = m2_from(S, n, Ns[w], bad);
+    }
+}
+
+template <typename R>
+static size_t small_grid_for(const DeviceInfo &dev, int N, int S) {
+    const uint64_t flat = (1ull << N) << N;
+    const long long tps = (long long)((flat + kTile - 1) >> kTileBits);
+    const int occ = sizeof(R) == 4 ? 2 : 1;
+    return (size_t)std::min<long long>(tps * S, (long long)dev.sms * occ);
+}
+
+BatchClass batch_class_layout(const DeviceInfo &dev, const Workspace &ws, int N, int S,
+                              sre_mode_t mode, const LargeCfg *tuned_half) {
+    BatchClass L;
+    L.N = N;
+    L.S = S;
+    const int eb = mode == SRE_MODE_FP64 ? 16 : 8;
+    if (N <= kTileBits) {
+        L.small_grid = (int)(eb == 8 ? small_grid_for<float>(dev, N, S) : small_grid_for<double>(dev, N, S));
+        const long long tps = (long long)((((1ull << N) << N) + kTile - 1) >> kTileBits);
+        L.cps_full = tps;  // tiles (= partials) per state
+        L.parts_n = (size_t)S * (size_t)tps;
+        return L;
+    }
+    L.cfg_full = choose_large_cfg(dev, N, eb, 0);
+    L.cfg_half = tuned_half ? *tuned_half : choose_large_cfg(dev, N, eb, 1);
+    L.cps_full = (long long)(((uint64_t)kTile + (1ull << L.cfg_full.C_log) - 1) >> L.cfg_full.C_log);
+    const uint64_t span = (1ull << N) - kTile;
+    L.cps_half = (long long)((span + (1ull << L.cfg_half.C_log) - 1) >> L.cfg_half.C_log);
+    L.parts_n = (size_t)S * (size_t)(L.cps_full + L.cps_half);
+    L.chunks_max = (size_t)S * (size_t)std::max(L.cps_full, L.cps_half);
+    (void)ws;
+    return L;
+}
+
+template <typename R>
+static cudaError_t enqueue_batch_class_t(const Workspace &ws, const DeviceInfo &dev,
+                                         const BatchClass &L, const void *const *d_ptrs,
+                                         double *parts, unsigned *counters, size_t chunk_cap,
+                                         cudaStream_t st, long long wait_ns) {
+    cudaError_t e;
+    const int N = L.N;
+    if (N <= kTileBits) {
+        int np = 0;
+        e = launch_small<R>(N, nullptr, d_ptrs, L.S, 0, 1ull << N, parts + L.parts_off,
+                            (int)L.parts_n, dev, st, &np, L.small_grid);
+        ws.launches += 1;
+        return e;
+    }
+    size_t off = L.parts_off;
+    for (int half = 0; half <= 1; ++half) {
+        const LargeCfg &c = half ? L.cfg_half : L.cfg_full;
+        const long long cps = half ? L.cps_half : L.cps_full;
+        if (!large_cfg_fits(ws, c, N, half)) return cudaErrorInvalidValue;
+        const uint64_t xb = half ? (uint64_t)kTile : 0, xe = half ? (1ull << N) : (uint64_t)kTile;
+        LargeArgs A;
+        A.psi = nullptr;
+        A.psis = d_ptrs;
+        A.chunks_per_state = cps;
+        A.N = N;
+        A.half = half;
+        A.h2 = N - kTileBits - half;
+        A.x_begin = xb;
+        A.x_end = xe;
+        A.x0 = xb;  // kTile and 0 are chunk-aligned
+        A.C_log = c.C_log;
+        A.R = c.R;
+        A.G2_log = std::min(c.G2_log, A.h2);
+        A.B1_log = std::max(0, std::min(c.B1_log, A.h2));
+        A.n_chunks = cps * L.S;
+        A.D = (int)std::max<long long>(1, std::min<long long>(std::min(c.D, c.R - 1), A.n_chunks));
+        A.P1 = 1 << (A.h2 - A.B1_log);
+        A.P2 = (1 << c.C_log) << (A.h2 - A.G2_log);
+        A.n_items = A.n_chunks * (long long)(A.P1 + A.P2);
+        if ((size_t)A.n_chunks > chunk_cap) return cudaErrorInvalidValue;
+        A.scratch = ws.scratch;
+        A.item_part = ws.item_part;
+        A.chunk_sum = parts + off;
+        A.done1 = counters;
+        A.done2 = counters + chunk_cap;
+        A.freed = counters + 2 * chunk_cap;
+        A.work = ws.work;
+        A.per_x = nullptr;
+        A.status = ws.status;
+        A.wait_ns = wait_ns;
+        if ((e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * 3 * chunk_cap, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(ws.work, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        const int grid = (int)std::max<long long>(1, std::min<long long>(c.grid, A.n_items));
+        e = half ? launch_large<R, true>(A, grid, st) : launch_large<R, false>(A, grid, st);
+        if (e != cudaSuccess) return e;
+        ws.launches += 1;
+        off += (size_t)A.n_chunks;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_batch_class(const Workspace &ws, const DeviceInfo &dev, const BatchClass &L,
+                                const void *const *d_ptrs, double *parts, unsigned *counters,
+                                size_t chunk_cap, sre_mode_t mode, cudaStream_t st,
+                                long long wait_ns) {
+    if (mode == SRE_MODE_FP64)
+        return enqueue_batch_class_t<double>(ws, dev, L, d_ptrs, parts, counters, chunk_cap, st, wait_ns);
+    return enqueue_batch_class_t<float>(ws, dev, L, d_ptrs, parts, counters, chunk_cap, st, wait_ns);
+}
+
+cudaError_t enqueue_batch_norm(const Workspace &ws, const void *const *d_ptrs, const int *d_Ns,
+                               int count, double *npart, int *flags, sre_mode_t mode,
+                               cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(flags, 0, sizeof(int) * count, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws.status, 0, sizeof(int), st)) != cudaSuccess) return e;
+    const dim3 grid(kNormBlocks, count);
+    if (mode == SRE_MODE_FP64)
+        k_norm_batch<double><<<grid, kThreads, 0, st>>>(d_ptrs, d_Ns, npart, flags);
+    else
+        k_norm_batch<float><<<grid, kThreads, 0, st>>>(d_ptrs, d_Ns, npart, flags);
+    ws.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_batch_finalize(const Workspace &ws, const void *seg, const double *parts,
+                                   const double *npart, const int *flags, const int *d_Ns,
+                                   const int *d_out_index, int count, double *m2_out,
+                                   cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = (count * 32 + threads - 1) / threads;
+    k_finalize_batch<<<blocks, threads, 0, st>>>(reinterpret_cast<const longlong4 *>(seg), parts, npart,
+                                                 kNormBlocks, flags, d_Ns, d_out_index, count,
+                                                 ws.status, m2_out);
+    ws.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_convert(const void *src, sre_dtype_t from, void *dst, int N, cudaStream_t st) {
+    const uint64_t d = 1ull << N;
+    const int grid = (int)std::min<uint64_t>((d + kThreads - 1) / kThreads, 4096);
+    if (from == SRE_C64)
+        k_convert<double2, float2><<<grid, kThreads, 0, st>>>(reinterpret_cast<const float2 *>(src),
+                                                              reinterpret_cast<double2 *>(dst), d);
+    else
+        k_convert<float2, double2><<<grid, kThreads, 0, st>>>(reinterpret_cast<const double2 *>(src),
+                                                              reinterpret_cast<float2 *>(dst), d);
+    return cudaGetLastError();
 }
 
 }  // namespace sre

@@ -213,6 +213,15 @@ SRE_API sre_status_t sre_sum4_range(sre_plan_t plan, const void *d_state, int N,
 SRE_API sre_status_t sre_m2_batched(sre_plan_t plan, const void *const *d_states, const int *Ns,
                             int count, sre_stream_t stream, double *d_m2_out);
 
+/*
+ * Failure-detection self test: launch one CTA that waits, with the same
+ * bounded wait the two-pass kernel uses, on a device counter that nothing
+ * increments.  The wait gives up after wait_ns of GPU time and the call
+ * returns the status the kernel recorded (SRE_ETIMEDOUT when the bound
+ * works).  SYNCHRONOUS on `stream`; the device context stays usable.
+ */
+SRE_API sre_status_t sre_selftest_wait_timeout(uint64_t wait_ns, sre_stream_t stream);
+
 /* ----------------------------------------------------------------------- */
 /* Serving: continuous batching of M2 requests of mixed N.                  */
 /* ----------------------------------------------------------------------- */

@@ -18,6 +18,7 @@ import threading
 
 __all__ = [
     "SreError", "Plan", "Server", "m2", "m2_batched", "library_path", "load_library",
+    "selftest_wait_timeout",
     "MODES", "DTYPES", "STATUS", "MAX_QUBITS",
 ]
 
@@ -101,6 +102,7 @@ def _declare(lib):
         "sre_m2_host": (S, [_vp, _vp, _i, _vp, _dp]),
         "sre_sum4_range": (S, [_vp, _vp, _i, _u64, _u64, _vp, _vp, _vp]),
         "sre_m2_batched": (S, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), _i, _vp, _vp]),
+        "sre_selftest_wait_timeout": (S, [_u64, _vp]),
         "sre_server_cfg_default": (None, [ctypes.POINTER(ServerCfg)]),
         "sre_server_create": (S, [ctypes.POINTER(ServerCfg), ctypes.POINTER(_vp)]),
         "sre_server_submit": (S, [_vp, _vp, _i, _i, _i, ctypes.POINTER(_u64)]),
@@ -324,6 +326,12 @@ class Plan:
         _check(load_library().sre_m2_batched(self._h, ptrs, Ns, n, _stream_handle(stream),
                                              ctypes.c_void_p(out.data_ptr())), "sre_m2_batched")
         return out
+
+
+def selftest_wait_timeout(wait_ns: int = 200_000_000, stream=None) -> int:
+    """sre_selftest_wait_timeout: status of a device wait that nothing satisfies
+    (SRE_ETIMEDOUT = 7 when the bound works)."""
+    return int(load_library().sre_selftest_wait_timeout(int(wait_ns), _stream_handle(stream)))
 
 
 _plans: dict = {}

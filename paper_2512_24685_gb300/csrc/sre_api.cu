@@ -424,6 +424,13 @@ sre_status_t sre_sum4_range(sre_plan_t p, const void *d_state, int N, uint64_t x
     return e == cudaSuccess ? SRE_OK : cuda_fail(e);
 }
 
+sre_status_t sre_selftest_wait_timeout(uint64_t wait_ns, sre_stream_t stream) {
+    int st = 0;
+    cudaError_t e = sre::run_wait_selftest((long long)wait_ns, (cudaStream_t)stream, &st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return st == -1 ? SRE_OK : (sre_status_t)st;
+}
+
 sre_status_t sre_m2_batched(sre_plan_t p, const void *const *d_states, const int *Ns, int count,
                             sre_stream_t stream, double *d_m2_out) {
     if (!p || !d_states || !Ns || !d_m2_out || count < 1 || count > 65535) return SRE_EINVAL;

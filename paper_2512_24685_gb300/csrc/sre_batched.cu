@@ -133,7 +133,7 @@ static cudaError_t enqueue_entry(BatchedContext *ctx, const Workspace &ws, const
 cudaError_t batched_run(BatchedContext *ctx, const Workspace &ws, const DeviceInfo &dev,
                         const void *const *d_states, const int *Ns, int count, sre_dtype_t dtype,
                         sre_mode_t mode, cudaStream_t stream, double *d_m2_out, long long wait_ns,
-                        const LargeCfg *const *tuned_half) {
+                        const LargeCfg *const *tuned_half, bool capture) {
     cudaError_t e;
     // ---- replay an existing graph for an identical batch
     for (size_t k = 0; k < ctx->graphs.size(); ++k) {
@@ -245,6 +245,12 @@ cudaError_t batched_run(BatchedContext *ctx, const Workspace &ws, const DeviceIn
     if ((e = enqueue_entry(ctx, ws, dev, g, classes, order, dtype, chunk_cap, stream, wait_ns)) != cudaSuccess)
         return e;
     g.launches = ws.launches - l0;
+    if (!capture) {
+        // one-off batch (e.g. a server unit): keep no entry around
+        free_entry(g);
+        ctx->graphs.pop_back();
+        return cudaSuccess;
+    }
     cudaStreamCaptureStatus cs;
     if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return cudaSuccess;
     if (stream == 0 || stream == cudaStreamLegacy) return cudaSuccess;  // not capturable

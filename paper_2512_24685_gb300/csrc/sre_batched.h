@@ -18,7 +18,7 @@ void batched_destroy(BatchedContext *ctx);
 cudaError_t batched_run(BatchedContext *ctx, const Workspace &ws, const DeviceInfo &dev,
                         const void *const *d_states, const int *Ns, int count, sre_dtype_t dtype,
                         sre_mode_t mode, cudaStream_t stream, double *d_m2_out, long long wait_ns,
-                        const LargeCfg *const *tuned_half);
+                        const LargeCfg *const *tuned_half, bool capture = true);
 
 // Tensor-core split-precision modes (BF16 / FP16 / TF32 hi-lo Hadamard stages).
 bool tc_mode_available(sre_mode_t mode);

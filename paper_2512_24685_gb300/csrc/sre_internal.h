@@ -126,6 +126,9 @@ cudaError_t enqueue_batch_finalize(const Workspace &ws, const void *seg, const d
                                    cudaStream_t st);
 cudaError_t enqueue_convert(const void *src, sre_dtype_t from, void *dst, int N, cudaStream_t st);
 
+// Bounded-wait self test (see sre_selftest_wait_timeout).
+cudaError_t run_wait_selftest(long long wait_ns, cudaStream_t st, int *status_out);
+
 // Copy the result block to d_out2 = {S, n2} (for the range API).
 cudaError_t enqueue_copy_sums(const Workspace &ws, double *d_out2, cudaStream_t stream);
 

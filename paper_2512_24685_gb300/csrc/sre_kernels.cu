@@ -810,6 +810,33 @@ cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d
                                cfg_override);
 }
 
+// --------------------------------------------------------- wait self test
+
+// One thread waits on a counter nothing increments; records the outcome.
+__global__ void k_wait_selftest(const unsigned *counter, int *status, long long wait_ns) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (wait_counter(counter, 1u, status, wait_ns)) atomicCAS(status, 0, -1);
+    }
+}
+
+cudaError_t run_wait_selftest(long long wait_ns, cudaStream_t st, int *status_out) {
+    unsigned *counter = nullptr;
+    int *status = nullptr;
+    cudaError_t e = cudaMalloc(&counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32, 0, st>>>(counter, status, wait_ns);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status_out, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(counter);
+    cudaFree(status);
+    return e;
+}
+
 // ------------------------------------------------------------------ batch
 
 // n2 of several states (state s = blockIdx.y, its size from Ns[s]);

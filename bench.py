@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-load", type=float, default=0.5)
+    ap.add_argument("--batch-states", type=int, default=512)
     return ap.parse_args()
 
 
@@ -202,6 +205,154 @@ def run_reference(args):
     return 0
 
 
+
+# ------------------------------------------------------------------ extras
+
+def _serving_pool(torch, W, n_lo=10, n_hi=20):
+    """One state per family (Haar, product, stabilizer, depth-8 brickwork) per
+    N, complex64, on the device."""
+    import numpy as np
+    pool = {}
+    for n in range(n_lo, n_hi + 1):
+        seed = W.config_seed(4, 10 * n)
+        pool[(n, 0)] = torch.from_numpy(W.haar_state(n, seed, np.complex64)).cuda()
+        pool[(n, 1)] = torch.from_numpy(W.product_state(n, seed + 1, np.complex64)[0]).cuda()
+        pool[(n, 2)] = W.stabilizer_state_torch(n, seed + 2, "cuda", dtype=torch.complex64).contiguous()
+        pool[(n, 3)] = W.brickwork_state_torch(n, 8, seed + 3, "cuda", dtype=torch.complex64).contiguous()
+    torch.cuda.synchronize()
+    return pool
+
+
+def _serving_trace(rate, seconds, seed, W):
+    import numpy as np
+    rng = W.rng_for(seed)
+    ns, p = W.serving_n_distribution()
+    t, trace = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        trace.append((t, int(rng.choice(ns, p=p)), int(rng.integers(4))))
+    return trace
+
+
+def run_serving(binding, torch, W, terms_per_s, seconds, load):
+    """Poisson arrivals at `load` x measured capacity through the server, and
+    the same trace with one synchronous launch per request (FIFO)."""
+    import threading as th
+    ns, p = W.serving_n_distribution()
+    mean_work = float(sum(pn * 4.0 ** n for n, pn in zip(ns, p)))
+    capacity = terms_per_s / mean_work
+    rate = load * capacity
+    pool = _serving_pool(torch, W)
+    trace = _serving_trace(rate, seconds, 4242, W)
+    out = {"arrival_rate_per_s": rate, "capacity_per_s": capacity, "load": load,
+           "seconds": seconds, "requests": len(trace), "mean_terms_per_request": mean_work,
+           "n_mix": "P(N) ~ 2^-(N-10)/2, N in 10..20; Haar/product/stabilizer/brickwork"}
+    with binding.Server(max_inflight=4, max_N=20, hbm_budget_bytes=16 << 30) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for (ta, n, fam) in trace:
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(pool[(n, fam)]))
+        for tk in tickets:
+            srv.wait(tk, 600000)
+        st = srv.stats()
+    out["server"] = {k: st[k] for k in ("p50_latency_ms", "p99_latency_ms", "mean_latency_ms",
+                                        "states_per_s", "pauli_terms_per_s", "completed", "failed",
+                                        "rejected", "peak_resident_bytes")}
+    # one launch per request, FIFO, same arrivals
+    lat = []
+    plans = {}
+    q, lock, done_ev = [], th.Lock(), th.Event()
+
+    def worker():
+        idx = 0
+        while idx < len(trace):
+            with lock:
+                ready = idx < len(q)
+            if not ready:
+                time.sleep(0.0002)
+                continue
+            (ta_abs, n, fam) = q[idx]
+            pl = plans.get(n)
+            if pl is None:
+                pl = plans[n] = binding.Plan(n, "c64")
+            pl.m2(pool[(n, fam)])
+            lat.append((time.perf_counter() - ta_abs) * 1000.0)
+            idx += 1
+        done_ev.set()
+
+    w = th.Thread(target=worker)
+    w.start()
+    t0 = time.perf_counter()
+    for (ta, n, fam) in trace:
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        with lock:
+            q.append((time.perf_counter(), n, fam))
+    done_ev.wait()
+    w.join()
+    span = max(1e-9, time.perf_counter() - t0)
+    lat.sort()
+    out["one_launch_per_request"] = {
+        "p50_latency_ms": lat[len(lat) // 2] if lat else None,
+        "p99_latency_ms": lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))] if lat else None,
+        "states_per_s": len(lat) / span}
+    for pl in plans.values():
+        pl.close()
+    return out
+
+
+def run_batched(binding, torch, W, count):
+    """The uneven batched workload: `count` brickwork states, N ~ U{12..18},
+    depth ~ U{1..32}, one sre_m2_batched submission replayed from its graph."""
+    spec = W.uneven_batch_spec(count=count)
+    states = [W.brickwork_state_torch(n, t, s, "cuda", dtype=torch.complex64).contiguous()
+              for n, t, s in spec]
+    terms = float(sum(4.0 ** n for n, _, _ in spec))
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with binding.Plan(18, "c64") as plan, torch.cuda.stream(side):
+        for n in (18, 17):
+            plan.autotune(n)
+        out = torch.empty(count, dtype=torch.float64, device="cuda")
+        plan.m2_batched(states, out=out)  # eager run + graph capture
+        plan.m2_batched(states, out=out)  # first replay
+        side.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = plan.launch_count()
+        e0.record(side)
+        plan.m2_batched(states, out=out)
+        e1.record(side)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = plan.launch_count() - l0
+    return {"states": count, "pauli_terms": terms, "ms": ms, "states_per_s": count / (ms / 1e3),
+            "pauli_terms_per_s": terms / (ms / 1e3), "gpu_launches": launches,
+            "workload": "brickwork Haar circuits on |0^N>, N ~ U{12..18}, depth ~ U{1..32}, complex64, FP32"}
+
+
+def run_fp64_check(binding, torch, W, N=16):
+    import numpy as np
+    psi = W.haar_state(N, W.config_seed(2, 1), np.complex128)
+    t = torch.from_numpy(psi).cuda()
+    res = {"N": N}
+    for mode in ("fp64", "fp32"):
+        with binding.Plan(N, "c128", mode) as p:
+            p.m2(t)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m = p.m2(t)
+            res[f"{mode}_ms"] = (time.perf_counter() - t0) * 1e3
+            res[f"m2_{mode}"] = m
+    res["abs_diff_fp32_vs_fp64"] = abs(res["m2_fp32"] - res["m2_fp64"])
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args):
@@ -340,6 +491,22 @@ def run_gpu(args):
         v, cores, sample = cpu_oracle_sample(N, args.cpu_seconds, W.config_seed(CONFIG_INDEX, 0))
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
+    extras = {}
+    if not args.no_extras:
+        try:
+            extras["serving"] = run_serving(binding, torch, W, value / world, args.serve_seconds,
+                                            args.serve_load)
+        except Exception as exc:  # reported, not hidden
+            extras["serving"] = {"error": repr(exc)}
+        try:
+            extras["batched"] = run_batched(binding, torch, W, args.batch_states)
+        except Exception as exc:
+            extras["batched"] = {"error": repr(exc)}
+        try:
+            extras["fp64_check"] = run_fp64_check(binding, torch, W)
+        except Exception as exc:
+            extras["fp64_check"] = {"error": repr(exc)}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
@@ -353,6 +520,10 @@ def run_gpu(args):
         "gpu_launches": int(launches), "wall_s": wall,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
     }
+    if extras.get("serving") and "server" in extras["serving"]:
+        line["serve_p50_ms"] = extras["serving"]["server"]["p50_latency_ms"]
+        line["serve_p99_ms"] = extras["serving"]["server"]["p99_latency_ms"]
+    line["extras"] = extras
     print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:

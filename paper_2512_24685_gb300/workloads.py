@@ -166,6 +166,33 @@ def brickwork_state_torch(N: int, depth: int, seed: int, device, dtype=None):
     return psi if dtype is None else psi.to(dtype)
 
 
+def stabilizer_state_torch(N: int, seed: int, device, depth: int | None = None, dtype=None):
+    """stabilizer_state on a torch device (same gate sequence, complex128)."""
+    import torch
+    rng = rng_for(seed)
+    depth = 2 * N if depth is None else depth
+    psi = torch.zeros(1 << N, dtype=torch.complex128, device=device)
+    psi[0] = 1.0
+    cl = [torch.as_tensor(g, dtype=torch.complex128, device=device) for g in _CLIFF1]
+    cnot = torch.as_tensor(_CNOT, dtype=torch.complex128, device=device)
+    for layer in range(depth):
+        for q in range(N):
+            U = cl[rng.integers(len(_CLIFF1))]
+            v = psi.reshape(1 << (N - q - 1), 2, 1 << q)
+            psi = torch.einsum("ab,ibj->iaj", U, v).reshape(-1)
+        for q in range(layer % 2, N - 1, 2):
+            v = psi.reshape(1 << (N - q - 2), 4, 1 << q)
+            psi = torch.einsum("ab,ibj->iaj", cnot, v).reshape(-1)
+    return psi if dtype is None else psi.to(dtype)
+
+
+def serving_n_distribution(n_lo: int = 10, n_hi: int = 20):
+    """P(N) proportional to 2^{-(N - n_lo)/2} on {n_lo..n_hi} (the serving mix)."""
+    ns = np.arange(n_lo, n_hi + 1)
+    w = 2.0 ** (-(ns - n_lo) / 2.0)
+    return ns, w / w.sum()
+
+
 def mixed_n16_batch(config_index: int = 1, N: int = 16, per_kind: int = 16,
                     depth: int = 8, dtype=np.complex64):
     """The four-family N=16 batch: `per_kind` each of Haar, product (with

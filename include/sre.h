@@ -214,6 +214,26 @@ SRE_API sre_status_t sre_m2_batched(sre_plan_t plan, const void *const *d_states
                             int count, sre_stream_t stream, double *d_m2_out);
 
 /*
+ * M2 of one complex64 state (FP32 arithmetic, device output) WITHOUT ANY
+ * ALLOCATION -- for callers that cannot allocate device or host memory at
+ * the point of the call (inside a region where cudaMalloc is unsafe or
+ * forbidden, under a fixed memory budget, ...).  The paper has no
+ * counterpart; this is an interface variant of sre_m2_async.
+ *   d_state: device buffer of 2^N interleaved (re, im) float pairs, 8-byte
+ *            aligned, 1 <= N <= SRE_NOALLOC_MAX_QUBITS (16); larger N is
+ *            rejected with SRE_EINVAL before anything is launched.
+ *   d_m2:    device double receiving M2 (NaN for a zero / non-finite state).
+ * Asynchronous on `stream`.  Its only scratch is one fixed module array of
+ * about 5.4 MB that every GPU loading the library holds until exit; the
+ * first call with a device current looks up that array's address and must
+ * not be made during a stream capture.  Every call shares the array, so
+ * calls whose work overlaps on the GPU race; calls ordered on the GPU are
+ * safe.  Returns SRE_EINVAL, SRE_EALIGN or SRE_ECUDA on error.
+ */
+#define SRE_NOALLOC_MAX_QUBITS 16
+SRE_API sre_status_t sre_m2_noalloc(const void *d_state, int N, sre_stream_t stream, double *d_m2);
+
+/*
  * Failure-detection self test: launch one CTA that waits, with the same
  * bounded wait the two-pass kernel uses, on a device counter that nothing
  * increments.  The wait gives up after wait_ns of GPU time and the call

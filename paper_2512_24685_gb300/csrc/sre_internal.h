@@ -129,6 +129,13 @@ cudaError_t enqueue_convert(const void *src, sre_dtype_t from, void *dst, int N,
 // Bounded-wait self test (see sre_selftest_wait_timeout).
 cudaError_t run_wait_selftest(long long wait_ns, cudaStream_t st, int *status_out);
 
+// FP32 M2 of a complex64 state with given two-pass configurations for the
+// shifts below 4096 and the halved shifts; allocates nothing (the workspace
+// pointers may point into preassigned memory).
+cudaError_t enqueue_m2_fixed(const Workspace &ws, const DeviceInfo &dev, const void *psi, int N,
+                             const LargeCfg &cfg_full, const LargeCfg &cfg_half, cudaStream_t st,
+                             double *d_m2, long long wait_ns);
+
 // Copy the result block to d_out2 = {S, n2} (for the range API).
 cudaError_t enqueue_copy_sums(const Workspace &ws, double *d_out2, cudaStream_t stream);
 

@@ -780,6 +780,53 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
     return cudaGetLastError();
 }
 
+// M2 of one complex64 state in FP32 with fixed two-pass configurations for
+// both shift ranges (no allocation, no autotuning): used by callers that
+// hand in preassigned scratch.  Same kernels and launch sequence as the
+// FP32 single-state path.
+cudaError_t enqueue_m2_fixed(const Workspace &ws, const DeviceInfo &dev, const void *psi, int N,
+                             const LargeCfg &cfg_full, const LargeCfg &cfg_half, cudaStream_t st,
+                             double *d_m2, long long wait_ns) {
+    using R = float;
+    cudaError_t e;
+    const uint64_t d = 1ull << N;
+    if ((e = cudaMemsetAsync(ws.flags, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws.status, 0, sizeof(int), st)) != cudaSuccess) return e;
+    k_norm<R><<<kNormBlocks, kThreads, 0, st>>>(reinterpret_cast<const v2_t<R> *>(psi), d, ws.npart,
+                                                ws.flags);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    long long nparts = 0, seg1 = 0;
+    const double *parts = nullptr;
+    if (N <= kTileBits) {
+        int np = 0;
+        if ((e = launch_small<R>(N, psi, nullptr, 1, 0, d, ws.part, ws.part_cap, dev, st, &np)) != cudaSuccess)
+            return e;
+        parts = ws.part;
+        nparts = seg1 = np;
+    } else {
+        if ((e = cudaMemsetAsync(ws.counters, 0, sizeof(unsigned) * 3 * ws.chunk_cap, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(ws.work, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess) return e;
+        size_t chunks = 0;
+        for (int half = 0; half <= 1; ++half) {
+            const uint64_t xb = half ? (uint64_t)kTile : 0, xe = half ? d : (uint64_t)kTile;
+            LargeArgs a;
+            int grid = 0;
+            if ((e = make_large_args(&a, ws, dev, psi, N, xb, xe, half, 8, chunks, nullptr, wait_ns,
+                                     half ? &cfg_half : &cfg_full, &grid)) != cudaSuccess)
+                return e;
+            e = half ? launch_large<R, true>(a, grid, st) : launch_large<R, false>(a, grid, st);
+            if (e != cudaSuccess) return e;
+            chunks += (size_t)a.n_chunks;
+            if (!half) seg1 = (long long)chunks;
+        }
+        parts = ws.chunk_sum;
+        nparts = (long long)chunks;
+    }
+    k_finalize<<<1, 32, 0, st>>>(parts, 0, seg1, seg1, nparts - seg1, ws.npart, kNormBlocks, N, ws.flags,
+                                 ws.status, ws.result, d_m2);
+    return cudaGetLastError();
+}
+
 cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d_state,
                        sre_dtype_t dtype, int N, uint64_t x_begin, uint64_t x_end,
                        sre_mode_t mode, cudaStream_t stream, double *d_m2, double *d_per_x,

@@ -243,9 +243,9 @@ static sre_status_t enqueue_plan_cfg(sre_plan_t p, const void *d_state, int N, u
                                      uint64_t xe, cudaStream_t st, double *d_m2, double *d_per_x,
                                      sre::LargeCfg *cfg) {
     cudaError_t e;
-    if (sre::tc_mode_available(p->mode) && p->mode != SRE_MODE_FP32 && p->mode != SRE_MODE_FP64)
+    if (sre::tc_mode_available(p->mode))
         e = sre::tc_enqueue_m2(p->ws, p->dev, d_state, p->dtype, N, xb, xe, p->mode, st, d_m2,
-                               d_per_x, p->wait_ns);
+                               d_per_x, p->wait_ns, cfg);
     else
         e = sre::enqueue_m2(p->ws, p->dev, d_state, p->dtype, N, xb, xe, p->mode, st, d_m2,
                             d_per_x, p->wait_ns, cfg);

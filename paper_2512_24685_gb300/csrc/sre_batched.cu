@@ -271,15 +271,4 @@ cudaError_t batched_run(BatchedContext *ctx, const Workspace &ws, const DeviceIn
     return cudaSuccess;
 }
 
-bool tc_mode_available(sre_mode_t mode) {
-    (void)mode;
-    return false;
-}
-
-cudaError_t tc_enqueue_m2(const Workspace &, const DeviceInfo &, const void *, sre_dtype_t, int,
-                          uint64_t, uint64_t, sre_mode_t, cudaStream_t, double *, double *,
-                          long long) {
-    return cudaErrorNotSupported;
-}
-
 }  // namespace sre

@@ -79,6 +79,13 @@ cudaError_t query_device(DeviceInfo *info);
 // shifts, x >= 4096).
 LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half);
 
+// Tensor-core launch of the halved two-pass kernel (sre_tc.cu): tc_kind 1 =
+// BF16 hi/lo split, 2 = FP16 hi/lo split; cudaErrorNotSupported if the
+// pass-2 bit count has no tensor-core instantiation.
+struct LargeArgs;
+cudaError_t launch_large_tc(const LargeArgs &a, int grid, cudaStream_t st, int tc_kind);
+size_t tc_extra_smem_bytes();
+
 // Does a (possibly tuned) configuration fit the workspace allocation?
 bool large_cfg_fits(const Workspace &ws, const LargeCfg &c, int N, int half);
 

@@ -29,6 +29,7 @@
 #include <algorithm>
 
 #include "sre_internal.h"
+#include "sre_large.cuh"
 #include "sre_tile.cuh"
 
 namespace sre {
@@ -123,285 +124,6 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
         // block_sum's barriers also protect bufB before the next tile
         const double s = block_sum((double)sum_abs4<R>(v), red);
         if (tid == 0) part[g] = s;
-    }
-}
-
-// -------------------------------------------------------- N > 12: k_large
-
-// Work of one evaluation over shifts [x_begin, x_end), N > 12.
-//
-// Shifts are grouped in chunks of C = 2^C_log consecutive values (aligned, so
-// a chunk shares x_h = x >> 12 and, for halved chunks, the pivot bit).  A
-// chunk owns one slot of a ring of R scratch slots.  Its work items:
-//   pass 1, P1 = 2^(h2 - B1_log) items of 2^B1_log consecutive blocks t'_h,
-//           each for every shift of the chunk -- the XOR-shifted products of
-//           one 2^12 block of t, the 12 low transform bits, written to
-//           scratch[slot][shift][t'_h][z_l];
-//   pass 2, P2 items of 2^G2_log tiles: for one shift and a range of z-blocks,
-//           the 2^h2 blocks t'_h of each z-block are read back, the h2 high
-//           bits are transformed and |A|^4 is reduced.
-// Items are claimed from one counter in a lagged order -- step s holds the
-// pass-1 items of chunk s and the pass-2 items of chunk s - D -- so pass 2
-// rarely waits for pass 1; pass 1 of chunk c waits for slot c % R to be
-// released by chunk c - R (D < R keeps this deadlock-free: every item waits
-// only on items claimed before it).
-//
-// Halving (half = 1, shifts x >= 4096).  With pivot j = the highest set bit
-// of x, g_x(t ^ x) = conj(g_x(t)) pairs every t with t_j = 1 to one with
-// t_j = 0, and sum_z |A_x(z)|^4 = 16 sum_{z'} [(Re W(z'))^4 + (Im W(z'))^4]
-// where W is the (N-1)-bit transform of g_x restricted to t_j = 0.  Since
-// j >= 12, the restriction removes one high bit: block t'_h maps to
-// t_h = t'_h with a zero inserted at bit j - 12, and h2 = N - 13.
-struct LargeArgs {
-    const void *psi;           // the state (single-state launch)
-    const void *const *psis;   // or: states of one batch class (device array)
-    long long chunks_per_state;  // chunks of each state (batch class)
-    int N, h2;                 // h2: pass-2 transform bits (N - 12, or N - 13 halved)
-    int half;
-    uint64_t x_begin, x_end;   // evaluated shift range
-    uint64_t x0;               // x_begin rounded down to a chunk boundary
-    int C_log, R, D, G2_log, B1_log;
-    long long n_chunks;
-    int P1, P2;                // items per chunk in pass 1 / pass 2
-    long long n_items;
-    void *scratch;             // R * C * 2^(N - half) complex
-    double *item_part;         // R * P2
-    double *chunk_sum;         // n_chunks
-    unsigned *done1, *done2, *freed;  // n_chunks each
-    unsigned long long *work;
-    double *per_x;             // optional, indexed by x - x_begin
-    int *status;
-    long long wait_ns;
-};
-
-// Thread 0 waits until *p >= target.  Bounded by wait_ns of %globaltimer and
-// by an iteration cap; on expiry it records SRE_ETIMEDOUT and returns false.
-// Returns false as well if another CTA already recorded an error.
-__device__ bool wait_counter(const unsigned *p, unsigned target, int *status, long long wait_ns) {
-    const unsigned long long t0 = globaltimer_ns();
-    for (unsigned it = 0; it < (1u << 30); ++it) {
-        if (ld_acquire_u32(p) >= target) return true;
-        if (*(volatile int *)status != 0) return false;
-        if ((it & 31) == 31 && (long long)(globaltimer_ns() - t0) > wait_ns) break;
-        __nanosleep(64);
-    }
-    atomicCAS(status, 0, (int)SRE_ETIMEDOUT);
-    return false;
-}
-
-// item -> (chunk, index within its pass, pass) for the lagged order.
-__device__ __forceinline__ void decode_item(const LargeArgs &a, long long item, long long &chunk,
-                                            int &r, bool &pass1) {
-    const long long D = a.D, P1 = a.P1, P2 = a.P2, n = a.n_chunks;
-    if (item < D * P1) {
-        chunk = item / P1;
-        r = (int)(item - chunk * P1);
-        pass1 = true;
-        return;
-    }
-    item -= D * P1;
-    const long long mid = (n - D) * (P1 + P2);
-    if (item < mid) {
-        const long long s = item / (P1 + P2);
-        const int q = (int)(item - s * (P1 + P2));
-        if (q < P1) {
-            chunk = D + s;
-            r = q;
-            pass1 = true;
-        } else {
-            chunk = s;
-            r = q - (int)P1;
-            pass1 = false;
-        }
-        return;
-    }
-    item -= mid;
-    const long long s = item / P2;
-    chunk = n - D + s;
-    r = (int)(item - s * P2);
-    pass1 = false;
-}
-
-template <typename R, int H2, bool HALF>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(LargeArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    using V = v2_t<R>;
-    V *bufA = reinterpret_cast<V *>(smem_raw);  // warp-local round 0 -> 1 moves
-    V *bufB = bufA + kTileSlots;                 // round 1 -> 2 moves, alternating
-    V *bufC = bufB + kTileSlots;                 //   with bufC from tile to tile
-    __shared__ double red[kThreads / 32];
-    __shared__ long long s_item;
-    __shared__ int s_flag;
-    unsigned tcount = 0;  // tiles that used a round 1 -> 2 move (uniform)
-
-    const int tid = threadIdx.x;
-    const int lgx = a.N - (HALF ? 1 : 0);        // log2 scratch entries per shift
-    const int C = 1 << a.C_log;
-    const V *psi0 = reinterpret_cast<const V *>(a.psi);
-    V *scratch = reinterpret_cast<V *>(a.scratch);
-    constexpr int zsub_bits = kTileBits - H2;     // z entries per block in pass 2
-    const int ipx_log = H2 - a.G2_log;            // pass-2 items per shift (log2)
-
-    for (;;) {
-        if (tid == 0) s_item = (long long)atomicAdd(a.work, 1ull);
-        __syncthreads();
-        const long long item = s_item;
-        if (item >= a.n_items) break;
-        long long c;
-        int r;
-        bool pass1;
-        decode_item(a, item, c, r, pass1);
-        const int slot = (int)(c % a.R);
-        // batch class: chunk c belongs to state c / chunks_per_state
-        long long cl = c;
-        const V *psi = psi0;
-        if (a.psis) {
-            const long long sidx = c / a.chunks_per_state;
-            cl = c - sidx * a.chunks_per_state;
-            psi = reinterpret_cast<const V *>(a.psis[sidx]);
-        }
-        const uint64_t xc = a.x0 + ((uint64_t)cl << a.C_log);
-        V *slot_base = scratch + (size_t)slot * ((size_t)C << lgx);
-
-        if (pass1) {
-            // ---------------- pass 1: blocks t'_h in [r 2^B1, (r+1) 2^B1) of
-            // every shift in the chunk
-            if (tid == 0) {
-                s_flag = 1;
-                if (c >= a.R) s_flag = wait_counter(a.freed + (c - a.R), 1u, a.status, a.wait_ns);
-            }
-            __syncthreads();
-            if (!s_flag) break;
-            const uint64_t xh = xc >> kTileBits;
-            const int xl0 = (int)(xc & (kTile - 1));
-            const int jh = HALF ? (63 - __clzll((long long)xc)) - kTileBits : 0;
-            for (int kb = 0; kb < (1 << a.B1_log); ++kb) {
-                const int tp = (r << a.B1_log) + kb;
-                const int th = HALF ? (((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1))) : tp;
-                // Round-2 layout: thread tid holds t_l = i << 8 | tid of block th
-                // (own factors phi_t in registers); its partners t ^ x are
-                // t_l ^ xlow of block th ^ x_h, read coalesced (each warp load
-                // covers one aligned 256-entry run).
-                R ar[16], ai[16];
-                {
-                    const V *pa = psi + ((uint64_t)th << kTileBits) + tid;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const V va = __ldg(pa + (i << 8));
-                        ar[i] = va.x;
-                        ai[i] = va.y;
-                    }
-                }
-                const V *pb = psi + (((uint64_t)th ^ xh) << kTileBits);
-                for (int xl = 0; xl < C; ++xl) {
-                    const uint64_t x = xc + (uint64_t)xl;
-                    if (x < a.x_begin || x >= a.x_end) continue;
-                    const int xlow = xl0 + xl;
-                    const V *pbx = pb + (tid ^ (xlow & 255));
-                    const int q = xlow >> 8;
-                    cx_t<R> v[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const V b = __ldg(pbx + ((i ^ q) << 8));
-                        v[i] = conj_mul<R>(b.x, b.y, ar[i], ai[i]);  // conj(phi_{t^x}) * phi_t
-                    }
-                    V *bB = (tcount & 1) ? bufC : bufB;
-                    ++tcount;
-                    tile_fwht12_rev<R>(v, bufA, bB, tid);
-                    // output in round-0 layout (z_l = 16 tid + i) stored at the
-                    // bit-permuted position i << 8 | tid: coalesced stores; pass 2
-                    // only sums over z, so the order of z inside a block is free
-                    V *o = slot_base + ((size_t)xl << lgx) + ((size_t)tp << kTileBits) + tid;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) __stcg(o + (i << 8), Cx<R>::to(v[i]));
-                }
-            }
-            __syncthreads();
-            if (tid == 0) {
-                __threadfence();
-                atomicAdd(a.done1 + c, 1u);
-            }
-        } else {
-            // ---------------- pass 2: 2^G2 z-blocks of one shift
-            const int j = r;
-            const int xl = j >> ipx_log;
-            const int zb0 = (j & ((1 << ipx_log) - 1)) << a.G2_log;
-            if (tid == 0) s_flag = wait_counter(a.done1 + c, (unsigned)a.P1, a.status, a.wait_ns);
-            __syncthreads();
-            if (!s_flag) break;
-            __threadfence();
-            const uint64_t x = xc + (uint64_t)xl;
-            double acc = 0.0;
-            if (x >= a.x_begin && x < a.x_end) {
-                const V *xb = slot_base + ((size_t)xl << lgx);
-                for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
-                    const int zb = zb0 + gb;
-                    cx_t<R> v[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int e = elem<0>(tid, i);
-                        const int tp = e & ((1 << H2) - 1);
-                        const int zs = e >> H2;
-                        v[i] = Cx<R>::from(
-                            __ldcg(xb + ((size_t)tp << kTileBits) + (zb << zsub_bits) + zs));
-                    }
-                    V *bB = (tcount & 1) ? bufC : bufB;
-                    if (H2 > 8) ++tcount;
-                    tile_fwht<H2, R>(v, bufA, bB, tid);
-                    if (HALF)
-                        acc += 16.0 * (double)sum_re4_im4<R>(v);
-                    else
-                        acc += (double)sum_abs4<R>(v);
-                }
-            }
-            const double s = block_sum(acc, red);
-            // Every thread of the CTA is past the barriers of block_sum, so all
-            // loads of this item's tiles are complete: drop their lines from
-            // L2 without write-back (dead data; the next chunk in this slot
-            // rewrites them).  Needs whole 128-byte lines per z-block row.
-            constexpr int kLineElems = 128 / (int)sizeof(V);
-            if ((zsub_bits >= 0) && ((1 << zsub_bits) >= kLineElems) && x >= a.x_begin && x < a.x_end) {
-                const V *xb = slot_base + ((size_t)xl << lgx);
-                constexpr int lines_per_row = (1 << zsub_bits) / kLineElems;
-                constexpr int lines_per_tile = kTile / kLineElems;
-                for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
-                    const int zb = zb0 + gb;
-                    for (int L = tid; L < lines_per_tile; L += kThreads) {
-                        const int row = L / (lines_per_row > 0 ? lines_per_row : 1);
-                        const int seg = L - row * lines_per_row;
-                        discard_l2_line(xb + ((size_t)row << kTileBits) + (zb << zsub_bits) +
-                                        seg * kLineElems);
-                    }
-                }
-            }
-            if (tid == 0) {
-                a.item_part[(size_t)slot * a.P2 + j] = s;
-                __threadfence();
-                const unsigned old = atomicAdd(a.done2 + c, 1u);
-                s_flag = (old == (unsigned)a.P2 - 1u);
-            }
-            __syncthreads();
-            if (s_flag) {
-                // last pass-2 item of the chunk: per-shift and chunk sums in fixed order
-                __threadfence();
-                double ps = 0.0;
-                for (int q = tid; q < C; q += kThreads) {
-                    double sx = 0.0;
-                    const double *ip = a.item_part + (size_t)slot * a.P2 + ((size_t)q << ipx_log);
-                    for (int k = 0; k < (1 << ipx_log); ++k) sx += __ldcg(ip + k);
-                    const uint64_t xq = xc + (uint64_t)q;
-                    if (a.per_x && xq >= a.x_begin && xq < a.x_end) a.per_x[xq - a.x_begin] = sx;
-                    ps += sx;
-                }
-                const double cs = block_sum(ps, red);
-                if (tid == 0) {
-                    a.chunk_sum[c] = cs;
-                    __threadfence();
-                    atomicExch(a.freed + c, 1u);
-                }
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -718,7 +440,8 @@ cudaError_t enqueue_copy_sums(const Workspace &ws, double *d_out2, cudaStream_t 
 template <typename R>
 static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, const void *psi, int N,
                                 uint64_t x_begin, uint64_t x_end, cudaStream_t st, double *d_m2,
-                                double *d_per_x, long long wait_ns, LargeCfg *cfg_override) {
+                                double *d_per_x, long long wait_ns, LargeCfg *cfg_override,
+                                int tc_kind) {
     cudaError_t e;
     const uint64_t d = 1ull << N;
     if ((e = cudaMemsetAsync(ws.flags, 0, sizeof(int), st)) != cudaSuccess) return e;
@@ -761,7 +484,9 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
                                      d_per_x ? d_per_x + (xb - x_begin) : nullptr, wait_ns,
                                      cfg_override && half ? cfg_override : nullptr, &grid)) != cudaSuccess)
                 return e;
-            if (half)
+            if (half && tc_kind)
+                e = launch_large_tc(a, grid, st, tc_kind);
+            else if (half)
                 e = launch_large<R, true>(a, grid, st);
             else
                 e = launch_large<R, false>(a, grid, st);
@@ -850,11 +575,12 @@ cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d
         ws.launches += 1;
         psi = ws.conv;
     }
+    const int tc_kind = mode == SRE_MODE_BF16_SPLIT ? 1 : mode == SRE_MODE_FP16_SPLIT ? 2 : 0;
     if (fp64)
         return enqueue_m2_t<double>(ws, dev, psi, N, x_begin, x_end, stream, d_m2, d_per_x, wait_ns,
-                                    cfg_override);
+                                    cfg_override, 0);
     return enqueue_m2_t<float>(ws, dev, psi, N, x_begin, x_end, stream, d_m2, d_per_x, wait_ns,
-                               cfg_override);
+                               cfg_override, tc_kind);
 }
 
 // --------------------------------------------------------- wait self test

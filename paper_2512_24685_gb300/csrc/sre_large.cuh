@@ -211,7 +211,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
                     }
                     V *bB = (tcount & 1) ? bufC : bufB;
                     ++tcount;
-                    tile_fwht12_rev<R>(v, bufA, bB, tid);
+                    if constexpr (TC != kTcNone) {
+                        // bits 8-11 and 4-7 on CUDA cores, bits 0-3 as an MMA
+                        // with H_16; the A operand goes to the cross-warp
+                        // buffer this tile does not use (no one reads it now)
+                        reg_stages<2, 12, R>(v);
+                        relayout<2, 1, false, R>(v, bB, tid);
+                        reg_stages<1, 12, R>(v);
+                        relayout<1, 0, true, R>(v, bufA, tid);
+                        tc.a = reinterpret_cast<unsigned char *>(bB == bufB ? bufC : bufB);
+                        if (!tc_round0<TC>(v, tc, tid, a.wait_ns) && tid == 0)
+                            atomicCAS(a.status, 0, (int)SRE_ETIMEDOUT);
+                    } else {
+                        tile_fwht12_rev<R>(v, bufA, bB, tid);
+                    }
                     // output in round-0 layout (z_l = 16 tid + i) stored at the
                     // bit-permuted position i << 8 | tid: coalesced stores; pass 2
                     // only sums over z, so the order of z inside a block is free

@@ -67,3 +67,6 @@ def test_split_modes_agree_with_fp32_at_n20(sre, torch_cuda):
             vals[mode] = p.m2(psi)
     for mode in MODES:
         assert abs(vals[mode] - vals["fp32"]) <= 1e-6, vals
+        # a different arithmetic ran: the hi/lo MMA does not reproduce the
+        # FP32 butterflies bit for bit
+        assert vals[mode] != vals["fp32"], vals

@@ -336,6 +336,38 @@ def run_batched(binding, torch, W, count):
             "workload": "brickwork Haar circuits on |0^N>, N ~ U{12..18}, depth ~ U{1..32}, complex64, FP32"}
 
 
+def run_tensor_modes(binding, torch, W, N, fp32_ms, fp32_m2, peaks):
+    """The split-precision tensor-core forms beside the FP32 form: one timed
+    evaluation each (after a warm-up) of the same N = 20 state."""
+    import numpy as np
+    psi = torch.from_numpy(W.haar_state(N, W.config_seed(CONFIG_INDEX, 0), np.complex64)).cuda()
+    d = 1 << N
+    # executed MMA flops: every halved shift (x >= 4096) has 2^(N-1) complex
+    # entries, each a real and an imaginary row entry of a K = 32 (hi, lo)
+    # by N = 16 product: 2 * 32 * 16 / 16 = 64 flops per real entry
+    mma_flops = (d - 4096) * (d // 2) * 2 * 64.0
+    out = {}
+    for mode in ("bf16_split", "fp16_split"):
+        with binding.Plan(N, "c64", mode) as p:
+            p.autotune(N)
+            p.set_profiling(True)
+            p.m2(psi)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m = p.m2(psi)
+            wall = time.perf_counter() - t0
+            kms = p.last_kernel_ms()[0]
+        peak = peaks.get("bf16_tflops", 1900.0)
+        out[mode] = {"ms": wall * 1e3, "kernel_ms": kms, "pauli_terms_per_s": float(d) * d / wall,
+                     "m2": m, "abs_diff_vs_fp32": abs(m - fp32_m2),
+                     "mma_tflops_executed": mma_flops / (kms * 1e-3) / 1e12,
+                     "tensor_roofline_frac": mma_flops / (kms * 1e-3) / (peak * 1e12),
+                     "vs_fp32_time": (kms / fp32_ms) if fp32_ms else None}
+    out["note"] = ("last pass-1 round (tile bits 0-3) as tcgen05 MMA with exact +-1 H_16, "
+                   "hi/lo split operands, FP32 accumulate in TMEM; tensor peak = measured bf16 burst")
+    return out
+
+
 def run_fp64_check(binding, torch, W, N=16):
     import numpy as np
     psi = W.haar_state(N, W.config_seed(2, 1), np.complex128)
@@ -491,6 +523,7 @@ def run_gpu(args):
         v, cores, sample = cpu_oracle_sample(N, args.cpu_seconds, W.config_seed(CONFIG_INDEX, 0))
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
+    peaks, peak_src = load_peaks()
     extras = {}
     if not args.no_extras:
         try:
@@ -506,6 +539,11 @@ def run_gpu(args):
             extras["fp64_check"] = run_fp64_check(binding, torch, W)
         except Exception as exc:
             extras["fp64_check"] = {"error": repr(exc)}
+        try:
+            extras["tensor_modes"] = run_tensor_modes(binding, torch, W, N, statistics.mean(kern_ms),
+                                                      m2_val, peaks)
+        except Exception as exc:
+            extras["tensor_modes"] = {"error": repr(exc)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

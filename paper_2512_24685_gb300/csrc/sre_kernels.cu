@@ -222,7 +222,7 @@ bool large_cfg_fits(const Workspace &ws, const LargeCfg &c, int N, int half) {
     if (c.G2_log < 0 || c.G2_log > h2 || c.B1_log < 0 || c.B1_log > h2) return false;
     const size_t ring = (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)ws.elem_bytes << (N - half));
     const size_t P2 = ((size_t)1 << c.C_log) << (h2 - c.G2_log);
-    return ring <= ws.scratch_bytes && (size_t)c.R * P2 <= ws.item_part_cap;
+    return ring <= ws.scratch_bytes && (size_t)c.R * P2 * 8 <= ws.item_part_cap;
 }
 
 // Ring / chunk configuration for the two-pass kernel.  About grid / P1
@@ -312,7 +312,8 @@ cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int
                 const int h2 = n - kTileBits - half;
                 scratch = std::max(scratch, (size_t)c.R * ((size_t)1 << c.C_log) *
                                                 ((size_t)elem_bytes << (n - half)));
-                item_cap = std::max(item_cap, (size_t)std::max(c.R, kMaxRing) * ((size_t)8 << h2));
+                // R * P2 per-warp partials (8 warps, P2 <= 8 * 2^h2)
+                item_cap = std::max(item_cap, (size_t)std::max(c.R, kMaxRing) * ((size_t)8 << h2) * 8);
             }
             chunk_cap = std::max(chunk_cap, ((size_t)1 << n) + 4);
         }
@@ -416,7 +417,7 @@ static cudaError_t make_large_args(LargeArgs *a, const Workspace &ws, const Devi
     A.n_items = A.n_chunks * (long long)(A.P1 + A.P2);
     const size_t need_scratch = (size_t)c.R * ((size_t)1 << c.C_log) * ((size_t)elem_bytes << (N - half));
     if (need_scratch > ws.scratch_bytes || chunk_off + (size_t)A.n_chunks > ws.chunk_cap ||
-        (size_t)c.R * A.P2 > ws.item_part_cap)
+        (size_t)c.R * A.P2 * 8 > ws.item_part_cap)
         return cudaErrorInvalidValue;
     A.scratch = ws.scratch;
     A.item_part = ws.item_part;
@@ -726,7 +727,8 @@ static cudaError_t enqueue_batch_class_t(const Workspace &ws, const DeviceInfo &
         A.P1 = 1 << (A.h2 - A.B1_log);
         A.P2 = (1 << c.C_log) << (A.h2 - A.G2_log);
         A.n_items = A.n_chunks * (long long)(A.P1 + A.P2);
-        if ((size_t)A.n_chunks > chunk_cap) return cudaErrorInvalidValue;
+        if ((size_t)A.n_chunks > chunk_cap || (size_t)A.R * A.P2 * 8 > ws.item_part_cap)
+            return cudaErrorInvalidValue;
         A.scratch = ws.scratch;
         A.item_part = ws.item_part;
         A.chunk_sum = parts + off;

@@ -24,7 +24,12 @@ using namespace dev;
 //           scratch[slot][shift][t'_h][z_l];
 //   pass 2, P2 items of 2^G2_log tiles: for one shift and a range of z-blocks,
 //           the 2^h2 blocks t'_h of each z-block are read back, the h2 high
-//           bits are transformed and |A|^4 is reduced.
+//           bits are transformed and |A|^4 is reduced, one FP64 partial per
+//           warp (item_part[(slot, item, warp)]).
+// Completion is counted per warp (P1 * 8 arrivals finish pass 1 of a chunk,
+// P2 * 8 pass 2), so no CTA barrier is needed at item boundaries; the warp
+// that completes a chunk's pass 2 sums its partials in fixed order, drops
+// the chunk's scratch lines from L2 and releases the ring slot.
 // Items are claimed from one counter in a lagged order -- step s holds the
 // pass-1 items of chunk s and the pass-2 items of chunk s - D -- so pass 2
 // rarely waits for pass 1; pass 1 of chunk c waits for slot c % R to be
@@ -114,9 +119,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
     V *bufA = reinterpret_cast<V *>(smem_raw);  // warp-local round 0 -> 1 moves
     V *bufB = bufA + kTileSlots;                 // round 1 -> 2 moves, alternating
     V *bufC = bufB + kTileSlots;                 //   with bufC from tile to tile
-    __shared__ double red[kThreads / 32];
-    __shared__ long long s_item;
-    __shared__ int s_flag;
+    __shared__ long long s_next[2];
+    __shared__ int s_stop[2];
     unsigned tcount = 0;  // tiles that used a round 1 -> 2 move (uniform)
 
     // tensor-core stage (TC != kTcNone, FP32 only): H_16 operand, mbarrier
@@ -146,11 +150,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
     constexpr int zsub_bits = kTileBits - H2;     // z entries per block in pass 2
     const int ipx_log = H2 - a.G2_log;            // pass-2 items per shift (log2)
 
-    for (;;) {
-        if (tid == 0) s_item = (long long)atomicAdd(a.work, 1ull);
-        __syncthreads();
-        const long long item = s_item;
-        if (item >= a.n_items) break;
+    const int warp = tid >> 5, lane = tid & 31;
+    constexpr int kWarps = kThreads / 32;
+    // Item claims are prefetched one item ahead through a two-entry slot;
+    // s_stop carries a recorded error so that the whole CTA stops together.
+    if (tid == 0) {
+        s_next[0] = (long long)atomicAdd(a.work, 1ull);
+        s_stop[0] = 0;
+    }
+    __syncthreads();
+    for (int par = 0;; par ^= 1) {
+        const long long item = s_next[par];
+        if (item >= a.n_items || s_stop[par]) break;
+        long long next = 0;
+        if (tid == 0) next = (long long)atomicAdd(a.work, 1ull);
         long long c;
         int r;
         bool pass1;
@@ -169,13 +182,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
 
         if (pass1) {
             // ---------------- pass 1: blocks t'_h in [r 2^B1, (r+1) 2^B1) of
-            // every shift in the chunk
-            if (tid == 0) {
-                s_flag = 1;
-                if (c >= a.R) s_flag = wait_counter(a.freed + (c - a.R), 1u, a.status, a.wait_ns);
+            // every shift in the chunk.  Each warp waits for the ring slot
+            // itself (an expired wait records SRE_ETIMEDOUT; the CTA then
+            // finishes this item on garbage and stops at the next claim).
+            if (c >= a.R) {
+                int ok = 1;
+                if (lane == 0) ok = wait_counter(a.freed + (c - a.R), 1u, a.status, a.wait_ns);
+                __syncwarp();
+                (void)ok;
             }
-            __syncthreads();
-            if (!s_flag) break;
             const uint64_t xh = xc >> kTileBits;
             const int xl0 = (int)(xc & (kTile - 1));
             const int jh = HALF ? (63 - __clzll((long long)xc)) - kTileBits : 0;
@@ -233,19 +248,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
                     for (int i = 0; i < 16; ++i) __stcg(o + (i << 8), Cx<R>::to(v[i]));
                 }
             }
-            __syncthreads();
-            if (tid == 0) {
-                __threadfence();
-                atomicAdd(a.done1 + c, 1u);
-            }
+            // per-warp completion: every lane's stores are fenced, then one arrival
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicAdd(a.done1 + c, 1u);
         } else {
-            // ---------------- pass 2: 2^G2 z-blocks of one shift
+            // ---------------- pass 2: 2^G2 z-blocks of one shift; per-warp
+            // wait, per-warp partial sums and per-warp completion
             const int j = r;
             const int xl = j >> ipx_log;
             const int zb0 = (j & ((1 << ipx_log) - 1)) << a.G2_log;
-            if (tid == 0) s_flag = wait_counter(a.done1 + c, (unsigned)a.P1, a.status, a.wait_ns);
-            __syncthreads();
-            if (!s_flag) break;
+            if (lane == 0) wait_counter(a.done1 + c, (unsigned)(a.P1 * kWarps), a.status, a.wait_ns);
+            __syncwarp();
             __threadfence();
             const uint64_t x = xc + (uint64_t)xl;
             double acc = 0.0;
@@ -271,52 +285,62 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
                         acc += (double)sum_abs4<R>(v);
                 }
             }
-            const double s = block_sum(acc, red);
-            // Every thread of the CTA is past the barriers of block_sum, so all
-            // loads of this item's tiles are complete: drop their lines from
-            // L2 without write-back (dead data; the next chunk in this slot
-            // rewrites them).  Needs whole 128-byte lines per z-block row.
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            // All warps' loads of this item are complete after this barrier:
+            // drop the item's scratch lines from L2 without write-back (dead
+            // data; the next chunk in this slot rewrites them).  The drops
+            // precede this item's arrivals, hence the slot's release.
+            __syncthreads();
             constexpr int kLineElems = 128 / (int)sizeof(V);
-            if ((zsub_bits >= 0) && ((1 << zsub_bits) >= kLineElems) && x >= a.x_begin && x < a.x_end) {
+            if (((1 << zsub_bits) >= kLineElems) && x >= a.x_begin && x < a.x_end) {
                 const V *xb = slot_base + ((size_t)xl << lgx);
-                constexpr int lines_per_row = (1 << zsub_bits) / kLineElems;
+                constexpr int lines_per_row = ((1 << zsub_bits) >= kLineElems) ? (1 << zsub_bits) / kLineElems : 1;
                 constexpr int lines_per_tile = kTile / kLineElems;
                 for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
                     const int zb = zb0 + gb;
                     for (int L = tid; L < lines_per_tile; L += kThreads) {
-                        const int row = L / (lines_per_row > 0 ? lines_per_row : 1);
+                        const int row = L / lines_per_row;
                         const int seg = L - row * lines_per_row;
-                        discard_l2_line(xb + ((size_t)row << kTileBits) + (zb << zsub_bits) +
-                                        seg * kLineElems);
+                        discard_l2_line(xb + ((size_t)row << kTileBits) + (zb << zsub_bits) + seg * kLineElems);
                     }
                 }
             }
-            if (tid == 0) {
-                a.item_part[(size_t)slot * a.P2 + j] = s;
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) {
+                a.item_part[(((size_t)slot * a.P2 + j) * kWarps) + warp] = acc;
                 __threadfence();
                 const unsigned old = atomicAdd(a.done2 + c, 1u);
-                s_flag = (old == (unsigned)a.P2 - 1u);
+                last = (old == (unsigned)(a.P2 * kWarps) - 1u);
             }
-            __syncthreads();
-            if (s_flag) {
-                // last pass-2 item of the chunk: per-shift and chunk sums in fixed order
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                // last warp of the chunk: per-shift and chunk sums in fixed
+                // order, then release the slot
                 __threadfence();
-                double ps = 0.0;
-                for (int q = tid; q < C; q += kThreads) {
+                const int per_x_items = (1 << ipx_log) * kWarps;
+                double cs = 0.0;
+                for (int q = 0; q < C; ++q) {
+                    const double *ip = a.item_part + ((size_t)slot * a.P2 + ((size_t)q << ipx_log)) * kWarps;
                     double sx = 0.0;
-                    const double *ip = a.item_part + (size_t)slot * a.P2 + ((size_t)q << ipx_log);
-                    for (int k = 0; k < (1 << ipx_log); ++k) sx += __ldcg(ip + k);
+                    for (int k = lane; k < per_x_items; k += 32) sx += __ldcg(ip + k);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sx += __shfl_down_sync(0xffffffffu, sx, o);
                     const uint64_t xq = xc + (uint64_t)q;
-                    if (a.per_x && xq >= a.x_begin && xq < a.x_end) a.per_x[xq - a.x_begin] = sx;
-                    ps += sx;
+                    if (lane == 0 && a.per_x && xq >= a.x_begin && xq < a.x_end) a.per_x[xq - a.x_begin] = sx;
+                    cs += sx;  // lane 0's value is the one used
                 }
-                const double cs = block_sum(ps, red);
-                if (tid == 0) {
+                if (lane == 0) {
                     a.chunk_sum[c] = cs;
                     __threadfence();
                     atomicExch(a.freed + c, 1u);
                 }
             }
+        }
+        if (tid == 0) {
+            s_next[par ^ 1] = next;
+            s_stop[par ^ 1] = (*(volatile int *)a.status != 0);
         }
         __syncthreads();
     }

@@ -295,11 +295,11 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
     std::vector<sre::LargeCfg> cands;
     for (int C_log = 0; C_log <= 3; ++C_log)
         for (int dm = 1; dm <= 2; ++dm)
-            for (int g = 0; g <= 2; ++g) {
+            for (int g = 0; g <= 3; ++g) {
                 sre::LargeCfg c = base;
                 c.C_log = C_log;
                 // bigger items when few shifts share a partner block
-                c.B1_log = std::min(h2, std::max(0, (g == 2 ? 3 : 2) - C_log));
+                c.B1_log = std::min(h2, std::max(0, (g >= 2 ? 3 : 2) - C_log));
                 const int items1 = 1 << (h2 - c.B1_log);
                 const int infl = std::max(1, (base.grid + items1 - 1) / items1);
                 c.D = std::min(dm * infl + 1, sre::kMaxRing / 2 - 1);

@@ -23,6 +23,7 @@
 // Every reduction has a fixed order, so results are bitwise reproducible and
 // do not depend on what else runs on the device.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -247,6 +248,9 @@ LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half
     while (C_log > 0 && (double)c.R * (double)(1 << C_log) * per_x > budget) --C_log;
     c.C_log = C_log;
     c.G2_log = std::min(C_log, h2);
+    // pass 2 staged through TMA (FP32, 5 <= h2 <= 8) overlaps the copy of
+    // tile g + 2 with tile g: give each item four tiles or more
+    if (elem_bytes == 8 && h2 >= 5 && h2 <= 8) c.G2_log = std::min(C_log + 2, h2);
     c.B1_log = 0;
     return c;
 }
@@ -367,13 +371,55 @@ static cudaError_t launch_small(int N, const void *psi, const void *const *psis,
     }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// The scratch ring of a launch as a 2-D FP32 array: 8192 columns (the 4096
+// complex entries of one block t'_h) by R * C * 2^h2 rows, 32 KB apart; boxes
+// of 32 FP32 columns (128 bytes, the swizzle span) by 2^h2 rows.
+cudaError_t encode_p2_tmap(LargeArgs &a) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    if (a.h2 < 5 || a.h2 > 8 || ((uintptr_t)a.scratch & 15)) return cudaErrorInvalidValue;
+    const cuuint64_t rows = (cuuint64_t)a.R << (a.C_log + a.h2);
+    if (rows > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {2ull * kTile, rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kTile * sizeof(float2)};
+    const cuuint32_t box[2] = {32u, 1u << a.h2};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.scratch, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <typename R, int H2, bool HALF>
 static cudaError_t launch_large_h(const LargeArgs &a, int grid, cudaStream_t st) {
-    const size_t smem = tile_smem_bytes(sizeof(v2_t<R>));
+    const size_t smem = large_smem_bytes<R, H2>(0);
     auto kern = k_large<R, H2, HALF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, smem, st>>>(a);
+    if constexpr (large_uses_tma<R, H2>()) {
+        LargeArgs b = a;
+        if ((e = encode_p2_tmap(b)) != cudaSuccess) return e;
+        kern<<<grid, kThreads, smem, st>>>(b);
+    } else {
+        kern<<<grid, kThreads, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

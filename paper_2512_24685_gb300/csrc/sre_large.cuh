@@ -1,10 +1,12 @@
 // sre_large.cuh -- the persistent two-pass kernel of libsre (N > 12),
 // shared by the CUDA-core translation unit and the tensor-core one.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "sre_internal.h"
+#include "sre_stage.cuh"
 #include "sre_tc.cuh"
 #include "sre_tile.cuh"
 
@@ -42,7 +44,12 @@ using namespace dev;
 // where W is the (N-1)-bit transform of g_x restricted to t_j = 0.  Since
 // j >= 12, the restriction removes one high bit: block t'_h maps to
 // t_h = t'_h with a zero inserted at bit j - 12, and h2 = N - 13.
+//
+// FP32 launches with 5 <= h2 <= 8 stage pass-2 tiles through TMA
+// (sre_stage.cuh): tmap then describes the scratch ring as a 2-D FP32 array
+// of 8192 columns (4096 complex per block t'_h) by R * C * 2^h2 rows.
 struct LargeArgs {
+    CUtensorMap tmap;          // pass-2 staging (encode_p2_tmap), else unused
     const void *psi;           // the state (single-state launch)
     const void *const *psis;   // or: states of one batch class (device array)
     long long chunks_per_state;  // chunks of each state (batch class)
@@ -112,23 +119,46 @@ __device__ __forceinline__ void decode_item(const LargeArgs &a, long long item, 
     pass1 = false;
 }
 
+// Pass 2 of this instantiation stages its tiles through TMA.
+template <typename R, int H2>
+__host__ __device__ constexpr bool large_uses_tma() {
+    return sizeof(R) == 4 && H2 >= 5 && H2 <= 8;
+}
+
+// Dynamic shared memory of k_large: three relayout buffers (the first two
+// double as the TMA stages of pass 2, hence 1024-byte alignment) and the
+// tensor-core extras.
+template <typename R, int H2>
+__host__ __device__ constexpr size_t large_smem_bytes(size_t tc_extra) {
+    return (size_t)3 * kTileSlots * sizeof(v2_t<R>) + tc_extra + (large_uses_tma<R, H2>() ? 1024 : 0);
+}
+
+// Host: encode LargeArgs::tmap for the launch's scratch ring.
+cudaError_t encode_p2_tmap(LargeArgs &a);
+
 template <typename R, int H2, bool HALF, int TC = kTcNone>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(LargeArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(const __grid_constant__ LargeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = v2_t<R>;
-    V *bufA = reinterpret_cast<V *>(smem_raw);  // warp-local round 0 -> 1 moves
-    V *bufB = bufA + kTileSlots;                 // round 1 -> 2 moves, alternating
-    V *bufC = bufB + kTileSlots;                 //   with bufC from tile to tile
+    constexpr bool kTma = large_uses_tma<R, H2>();
+    unsigned char *sbase = smem_raw;
+    if constexpr (kTma) sbase += (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    V *bufB = reinterpret_cast<V *>(sbase);  // round 1 -> 2 moves, alternating with
+    V *bufC = bufB + kTileSlots;             //   bufC from tile to tile; pass-2 stages
+    V *bufA = bufC + kTileSlots;             // warp-local moves
     __shared__ long long s_next[2];
     __shared__ int s_stop[2];
+    __shared__ __align__(8) uint64_t s_mbar[2];  // pass-2 stage barriers (kTma)
     unsigned tcount = 0;  // tiles that used a round 1 -> 2 move (uniform)
+    uint32_t sphase = 0;  // parity of the next completion of each stage (kTma)
+    uint32_t slost = 0;   // stages whose completion wait expired (kTma)
 
     // tensor-core stage (TC != kTcNone, FP32 only): H_16 operand, mbarrier
     // and TMEM after the three relayout buffers
     TcState tc;
     __shared__ uint32_t s_tmem;
     if constexpr (TC != kTcNone) {
-        unsigned char *extra = reinterpret_cast<unsigned char *>(bufC + kTileSlots);
+        unsigned char *extra = reinterpret_cast<unsigned char *>(bufA + kTileSlots);
         tc.b = extra;
         tc.mbar = smem_u32(extra + kTcBBytes);
         tc.phase = 0;
@@ -157,6 +187,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
     if (tid == 0) {
         s_next[0] = (long long)atomicAdd(a.work, 1ull);
         s_stop[0] = 0;
+        if constexpr (kTma) {
+            mbar_init(smem_u32(&s_mbar[0]), 1);
+            mbar_init(smem_u32(&s_mbar[1]), 1);
+        }
     }
     __syncthreads();
     for (int par = 0;; par ^= 1) {
@@ -258,11 +292,61 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
             const int j = r;
             const int xl = j >> ipx_log;
             const int zb0 = (j & ((1 << ipx_log) - 1)) << a.G2_log;
+            const uint64_t x = xc + (uint64_t)xl;
+            double acc = 0.0;
+            if constexpr (kTma) {
+                // One thread waits for the chunk's pass 1 and keeps two TMA
+                // tile copies in flight; every thread waits on the stage's
+                // mbarrier, reads the tile in layout A and transforms it.
+                if (x >= a.x_begin && x < a.x_end) {
+                    const int ntiles = 1 << a.G2_log;
+                    const int y = (int)(((size_t)slot * C + xl) << H2);
+                    int ok = 1;
+                    auto issue = [&](int g, int st) {
+                        const uint32_t mb = smem_u32(&s_mbar[st]);
+                        if (!ok) {
+                            mbar_arrive(mb);  // no copy: release the waiters on garbage
+                            return;
+                        }
+                        const uint32_t dst = smem_u32(st ? (void *)bufC : (void *)bufB);
+                        const int x0 = (zb0 + g) << (kTileBits - H2 + 1);  // FP32 column
+                        mbar_arrive_expect_tx(mb, (uint32_t)kStageBytes);
+#pragma unroll
+                        for (int b = 0; b < (1 << (8 - H2)); ++b)
+                            tma_load_2d(dst + (uint32_t)b * (128u << H2), &a.tmap, x0 + 32 * b, y, mb);
+                    };
+                    if (tid == 0) {
+                        ok = wait_counter(a.done1 + c, (unsigned)(a.P1 * kWarps), a.status, a.wait_ns);
+                        // pass-1 stores (acquired above) and this CTA's earlier
+                        // shared-memory accesses before the async-proxy copies
+                        fence_proxy_async();
+                        issue(0, 0);
+                        if (ntiles > 1) issue(1, 1);
+                    }
+                    const P2Lane pl = p2_lane<H2>(lane, warp);
+                    for (int gb = 0; gb < ntiles; ++gb) {
+                        const int st = gb & 1;
+                        if (!mbar_wait_bounded(smem_u32(&s_mbar[st]), (sphase >> st) & 1u, a.wait_ns)) {
+                            slost |= 1u << st;
+                            if (lane == 0) atomicCAS(a.status, 0, (int)SRE_ETIMEDOUT);
+                        }
+                        sphase ^= 1u << st;
+                        const unsigned char *stage = reinterpret_cast<const unsigned char *>(st ? bufC : bufB);
+                        const float s = p2_tile<H2, HALF>(stage, reinterpret_cast<float2 *>(bufA), pl);
+                        acc += (HALF ? 16.0 : 1.0) * (double)s;
+                        if (gb + 2 < ntiles) {
+                            __syncthreads();  // every thread has read stage st
+                            if (tid == 0) {
+                                fence_proxy_async();
+                                issue(gb + 2, st);
+                            }
+                        }
+                    }
+                }
+            } else {
             if (lane == 0) wait_counter(a.done1 + c, (unsigned)(a.P1 * kWarps), a.status, a.wait_ns);
             __syncwarp();
             __threadfence();
-            const uint64_t x = xc + (uint64_t)xl;
-            double acc = 0.0;
             if (x >= a.x_begin && x < a.x_end) {
                 const V *xb = slot_base + ((size_t)xl << lgx);
                 for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
@@ -284,6 +368,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
                     else
                         acc += (double)sum_abs4<R>(v);
                 }
+            }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -343,6 +428,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(Larg
             s_stop[par ^ 1] = (*(volatile int *)a.status != 0);
         }
         __syncthreads();
+    }
+    if constexpr (kTma) {
+        // a stage whose completion wait expired may still receive its copy:
+        // wait for it once more (bounded) before the CTA's memory is released
+        for (int st = 0; st < 2; ++st)
+            if (slost & (1u << st)) mbar_wait_bounded(smem_u32(&s_mbar[st]), ((sphase >> st) & 1u) ^ 1u, a.wait_ns);
     }
     if constexpr (TC != kTcNone) {
         tc_fence_before();

@@ -14,11 +14,17 @@ size_t tc_extra_smem_bytes() { return (size_t)kTcBBytes + 16; }
 
 template <int H2, int TC>
 static cudaError_t launch_tc_h(const LargeArgs &a, int grid, cudaStream_t st) {
-    const size_t smem = (size_t)3 * kTileSlots * sizeof(float2) + tc_extra_smem_bytes();
+    const size_t smem = large_smem_bytes<float, H2>(tc_extra_smem_bytes());
     auto kern = k_large<float, H2, true, TC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, smem, st>>>(a);
+    if constexpr (large_uses_tma<float, H2>()) {
+        LargeArgs b = a;
+        if ((e = encode_p2_tmap(b)) != cudaSuccess) return e;
+        kern<<<grid, kThreads, smem, st>>>(b);
+    } else {
+        kern<<<grid, kThreads, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

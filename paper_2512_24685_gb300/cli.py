@@ -3,6 +3,10 @@
     python -m paper_2512_24685_gb300.cli m2 --N 20 [--family haar] [--seed S] [--mode fp32]
     python -m paper_2512_24685_gb300.cli range --N 20 --x-begin B --count C [--per-x]
 
+Both take --tuning C_LOG,R,D,G2,B1 (the two-pass kernel's chunk size, ring
+slots, lag, pass-2 tiles and pass-1 blocks per item, logs base 2 where
+named so; -1 keeps the default) or --autotune (sre_plan_autotune first).
+
 `m2` evaluates M2 of one generated state; `range` evaluates the partial sum
 sum_{x in [B, B+C)} sum_z |<psi|X^x Z^z|psi>|^4 through sre_sum4_range (the
 shard of a state's work that one device takes when shifts are split).
@@ -43,6 +47,8 @@ def main(argv=None):
         p.add_argument("--dtype", default="c64", choices=["c64", "c128"])
         p.add_argument("--mode", default=None)
         p.add_argument("--repeat", type=int, default=1)
+        p.add_argument("--tuning", default=None, help="C_LOG,R,D,G2,B1 of the halved-shift launch")
+        p.add_argument("--autotune", action="store_true")
         if name == "range":
             p.add_argument("--x-begin", type=int, required=True)
             p.add_argument("--count", type=int, required=True)
@@ -55,6 +61,12 @@ def main(argv=None):
     psi = torch.from_numpy(_state(args)).cuda()
     out = {"cmd": args.cmd, "N": args.N, "family": args.family, "seed": args.seed}
     with binding.Plan(args.N, args.dtype, args.mode) as plan:
+        if args.tuning:
+            plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
+        elif args.autotune:
+            plan.autotune(args.N)
+        if args.tuning or args.autotune:
+            out["tuning"] = plan.get_tuning(args.N)
         t0 = time.perf_counter()
         for _ in range(args.repeat):
             if args.cmd == "m2":

@@ -287,28 +287,38 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
         if (e != cudaSuccess) return cuda_fail(e);
     }
     if ((e = sre::enqueue_fill_synthetic(p->tune_state, N, p->dtype, st)) != cudaSuccess) return cuda_fail(e);
-    // candidates around the in-flight estimate: chunk size, lag depth, pass-2 item size
+    // candidates: chunk size C, pass-2 tiles per item G2, pass-1 blocks per
+    // item B1, and a lag D of 1-3 times the lag steps the grid covers at
+    // once (one lag step claims the P1 + P2 items of a chunk)
     const int eb = elem_bytes_for_mode(p->mode);
     const sre::LargeCfg base = sre::choose_large_cfg(p->dev, N, eb, 1);
     const int h2 = N - sre::kTileBits - 1;
-    const int inflight = std::max(1, (base.grid + (1 << h2) - 1) >> h2);
     std::vector<sre::LargeCfg> cands;
+    auto add = [&](const sre::LargeCfg &c) {
+        for (const sre::LargeCfg &o : cands)
+            if (o.C_log == c.C_log && o.G2_log == c.G2_log && o.B1_log == c.B1_log && o.D == c.D) return;
+        if (sre::large_cfg_fits(p->ws, c, N, 1)) cands.push_back(c);
+    };
     for (int C_log = 0; C_log <= 3; ++C_log)
-        for (int dm = 1; dm <= 2; ++dm)
-            for (int g = 0; g <= 3; ++g) {
-                sre::LargeCfg c = base;
-                c.C_log = C_log;
-                // bigger items when few shifts share a partner block
-                c.B1_log = std::min(h2, std::max(0, (g >= 2 ? 3 : 2) - C_log));
-                const int items1 = 1 << (h2 - c.B1_log);
-                const int infl = std::max(1, (base.grid + items1 - 1) / items1);
-                c.D = std::min(dm * infl + 1, sre::kMaxRing / 2 - 1);
-                c.R = 2 * c.D + 1;
-                c.G2_log = std::min(h2, g == 0 ? C_log : C_log + g);
-                if (g == 0) c.B1_log = 0;
-                if (sre::large_cfg_fits(p->ws, c, N, 1)) cands.push_back(c);
-            }
-    (void)inflight;
+        for (int g = 0; g <= 3; ++g)
+            for (int b = 2; b <= 3; ++b)
+                for (int dm = 1; dm <= 3; ++dm) {
+                    sre::LargeCfg c = base;
+                    c.C_log = C_log;
+                    c.G2_log = std::min(h2, C_log + g);
+                    c.B1_log = std::min(h2, std::max(0, b - C_log));
+                    const int P1 = 1 << (h2 - c.B1_log);
+                    const int P2 = (1 << C_log) << (h2 - c.G2_log);
+                    const int steps = std::max(1, (base.grid + P1 + P2 - 1) / (P1 + P2));
+                    c.D = std::min(dm * steps + 1, sre::kMaxRing / 2 - 1);
+                    // ring of 2 D + 1 chunks, or as many as the scratch holds
+                    // (at least D + 2)
+                    const size_t per_chunk = ((size_t)eb << (N - 1)) << C_log;
+                    const int r_fit = (int)std::min<size_t>(p->ws.scratch_bytes / per_chunk, sre::kMaxRing);
+                    c.R = std::min(2 * c.D + 1, r_fit);
+                    if (c.R < c.D + 2) continue;
+                    add(c);
+                }
     if (cands.empty()) return SRE_OK;
     // a slice of halved shifts worth ~2^34 entries of work
     const uint64_t d = 1ull << N;

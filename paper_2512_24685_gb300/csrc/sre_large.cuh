@@ -125,6 +125,14 @@ __host__ __device__ constexpr bool large_uses_tma() {
     return sizeof(R) == 4 && H2 >= 5 && H2 <= 8;
 }
 
+// Pass 1 of this instantiation can take its block pairs by bulk copy (FP32
+// CUDA-core path; used at run time for one shift per chunk and 16-byte
+// aligned states).
+template <typename R, int TC>
+__host__ __device__ constexpr bool large_stages_pass1() {
+    return sizeof(R) == 4 && TC == kTcNone;
+}
+
 // Dynamic shared memory of k_large: three relayout buffers (the first two
 // double as the TMA stages of pass 2, hence 1024-byte alignment) and the
 // tensor-core extras.
@@ -141,6 +149,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = v2_t<R>;
     constexpr bool kTma = large_uses_tma<R, H2>();
+    constexpr bool kStage1 = large_stages_pass1<R, TC>();
     unsigned char *sbase = smem_raw;
     if constexpr (kTma) sbase += (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     V *bufB = reinterpret_cast<V *>(sbase);  // round 1 -> 2 moves, alternating with
@@ -148,10 +157,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
     V *bufA = bufC + kTileSlots;             // warp-local moves
     __shared__ long long s_next[2];
     __shared__ int s_stop[2];
-    __shared__ __align__(8) uint64_t s_mbar[2];  // pass-2 stage barriers (kTma)
+    // stage barriers: [0], [1] the pass-2 tile stages (kTma), [2] the pass-1
+    // block pair (kStage1)
+    __shared__ __align__(8) uint64_t s_mbar[3];
     unsigned tcount = 0;  // tiles that used a round 1 -> 2 move (uniform)
-    uint32_t sphase = 0;  // parity of the next completion of each stage (kTma)
-    uint32_t slost = 0;   // stages whose completion wait expired (kTma)
+    uint32_t sphase = 0;  // parity of the next completion of each barrier
+    uint32_t slost = 0;   // barriers whose completion wait expired
 
     // tensor-core stage (TC != kTcNone, FP32 only): H_16 operand, mbarrier
     // and TMEM after the three relayout buffers
@@ -187,9 +198,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
     if (tid == 0) {
         s_next[0] = (long long)atomicAdd(a.work, 1ull);
         s_stop[0] = 0;
-        if constexpr (kTma) {
-            mbar_init(smem_u32(&s_mbar[0]), 1);
-            mbar_init(smem_u32(&s_mbar[1]), 1);
+        if constexpr (kTma || kStage1) {
+            for (int k = 0; k < 3; ++k) mbar_init(smem_u32(&s_mbar[k]), 1);
         }
     }
     __syncthreads();
@@ -228,6 +238,67 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
             const uint64_t xh = xc >> kTileBits;
             const int xl0 = (int)(xc & (kTile - 1));
             const int jh = HALF ? (63 - __clzll((long long)xc)) - kTileBits : 0;
+            if (kStage1 && C == 1 && ((uintptr_t)psi & 15) == 0) {
+                // One shift per chunk and a 16-byte aligned state: the block
+                // t_h and its partner t_h ^ x_h arrive by two 32 KB bulk copies
+                // in the two stage buffers.  The products overwrite the own
+                // block in place (each thread rewrites only the entries it
+                // read) and that buffer serves the CTA-wide move; once it has
+                // been read back the next pair's copies are issued, so they
+                // overlap the rest of the tile.
+                if (xc >= a.x_begin && xc < a.x_end) {
+                    const int nb = 1 << a.B1_log;
+                    const uint32_t mb = smem_u32(&s_mbar[2]);
+                    V *own = bufB;
+                    const V *par = bufC;
+                    auto issue_pair = [&](int kb) {
+                        const int tp = (r << a.B1_log) + kb;
+                        const int th = HALF ? (((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1))) : tp;
+                        mbar_arrive_expect_tx(mb, 2u * kStageBytes);
+                        bulk_load(smem_u32(own), psi + ((uint64_t)th << kTileBits), kStageBytes, mb);
+                        bulk_load(smem_u32(par), psi + (((uint64_t)th ^ xh) << kTileBits), kStageBytes, mb);
+                    };
+                    if (tid == 0) {
+                        fence_proxy_async();
+                        issue_pair(0);
+                    }
+                    const int xlow = xl0;
+                    const int q = xlow >> 8;
+                    const int pl = tid ^ (xlow & 255);
+                    for (int kb = 0; kb < nb; ++kb) {
+                        const int tp = (r << a.B1_log) + kb;
+                        if (!mbar_wait_bounded(mb, (sphase >> 2) & 1u, a.wait_ns)) {
+                            slost |= 4u;
+                            if (lane == 0) atomicCAS(a.status, 0, (int)SRE_ETIMEDOUT);
+                        }
+                        sphase ^= 4u;
+                        cx_t<R> v[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const V b = par[((i ^ q) << 8) | pl];
+                            const V va = own[(i << 8) | tid];
+                            v[i] = conj_mul<R>(b.x, b.y, va.x, va.y);  // conj(phi_{t^x}) * phi_t
+                        }
+                        reg_stages<2, 12, R>(v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) own[(i << 8) | tid] = Cx<R>::to(v[i]);
+                        __syncthreads();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = Cx<R>::from(own[elem<1>(tid, i)]);
+                        __syncthreads();  // both stage buffers are free
+                        if (tid == 0 && kb + 1 < nb) {
+                            fence_proxy_async();
+                            issue_pair(kb + 1);
+                        }
+                        reg_stages<1, 12, R>(v);
+                        relayout<1, 0, true, R>(v, bufA, tid);
+                        reg_stages<0, 12, R>(v);
+                        V *o = slot_base + ((size_t)tp << kTileBits) + tid;
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) __stcg(o + (i << 8), Cx<R>::to(v[i]));
+                    }
+                }
+            } else
             for (int kb = 0; kb < (1 << a.B1_log); ++kb) {
                 const int tp = (r << a.B1_log) + kb;
                 const int th = HALF ? (((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1))) : tp;
@@ -429,10 +500,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
         }
         __syncthreads();
     }
-    if constexpr (kTma) {
+    if constexpr (kTma || kStage1) {
         // a stage whose completion wait expired may still receive its copy:
         // wait for it once more (bounded) before the CTA's memory is released
-        for (int st = 0; st < 2; ++st)
+        for (int st = 0; st < 3; ++st)
             if (slost & (1u << st)) mbar_wait_bounded(smem_u32(&s_mbar[st]), ((sphase >> st) & 1u) ^ 1u, a.wait_ns);
     }
     if constexpr (TC != kTcNone) {

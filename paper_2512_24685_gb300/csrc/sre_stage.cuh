@@ -211,6 +211,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tma
         : "memory");
 }
 
+// 1-D bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned)
+// from global memory into shared memory at dst, completing on mbar.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
 // Order this thread's earlier generic-proxy accesses (and those it has
 // observed through acquire / barrier) before its later async-proxy ones.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }

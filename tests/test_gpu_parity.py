@@ -147,6 +147,33 @@ def test_deterministic_bitwise(sre, torch_cuda):
         assert len(vals) == 1
 
 
+@pytest.mark.parametrize("N,tuning,xr", [
+    (14, (0, 9, 4, 1, 1), (0, 1 << 14)),
+    (17, (0, 15, 7, 2, 2), (0, 1 << 17)),
+    (20, (0, 23, 11, 2, 2), (4096 - 64, 4096 + 2048)),
+])
+def test_staged_and_register_pass1_agree(sre, torch_cuda, N, tuning, xr):
+    """One shift per chunk: a 16-byte aligned state takes its pass-1 block
+    pairs by bulk copy into shared memory, the same state at an 8-byte offset
+    by per-thread loads.  Both paths do the same arithmetic in the same
+    order, so the per-shift sums agree bit for bit."""
+    torch = torch_cuda
+    psi = torch.from_numpy(W.haar_state(N, 77, np.complex64)).cuda()
+    pad = torch.zeros((1 << N) + 1, dtype=torch.complex64, device="cuda")
+    pad[1:] = psi
+    shifted = pad[1:]
+    assert psi.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 8
+    with sre.Plan(N, "c64") as p:
+        p.set_tuning(*tuning)
+        out_a, px_a = p.sum4_range(psi, xr[0], xr[1], per_x=True)
+        out_b, px_b = p.sum4_range(shifted, xr[0], xr[1], per_x=True)
+        torch.cuda.synchronize()
+    assert torch.equal(px_a, px_b)
+    assert torch.equal(out_a, out_b)
+    ref = oracle.sum4_xorfwht(psi.cpu().numpy(), xr[1] - 1, xr[1])
+    assert abs(px_a[-1].item() - ref) <= 1e-5 * ref
+
+
 # -------------------------------------------------- full-size (N = 20) checks
 
 def test_n20_full_size_sampled(sre, torch_cuda):
@@ -157,6 +184,7 @@ def test_n20_full_size_sampled(sre, torch_cuda):
     psi = W.haar_state(N, W.config_seed(2, 0), np.complex64)
     t = dev(torch_cuda, psi)
     with sre.Plan(N, "c64") as p:
+        p.autotune(N)  # as bench.py does before timing
         m2 = p.m2(t)
         out, px = p.sum4_range(t, 0, 1 << N, per_x=True)
         torch_cuda.cuda.synchronize()

@@ -331,27 +331,48 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
         cudaEventDestroy(e0);
         return cuda_fail(e);
     }
+    // Two rounds: every candidate once on twice the slice (after one warm-up
+    // launch), then the fastest eight twice on four times the slice, which
+    // ranks the candidates in steady state.
+    sre_status_t s = SRE_OK;
+    auto time_cfg = [&](sre::LargeCfg c, uint64_t x_end, float *ms) -> sre_status_t {
+        cudaEventRecord(e0, st);
+        sre_status_t r = enqueue_plan_cfg(p, p->tune_state, N, xb, x_end, st, nullptr, nullptr, &c);
+        cudaEventRecord(e1, st);
+        if (r != SRE_OK) return r;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return cuda_fail(e);
+        cudaEventElapsedTime(ms, e0, e1);
+        return SRE_OK;
+    };
+    std::vector<std::pair<float, size_t>> screen;
+    {
+        float ms = 0.f;
+        const uint64_t xe1 = std::min<uint64_t>(xb + 2 * n, d);
+        s = time_cfg(cands[0], xe, &ms);  // warm-up
+        for (size_t k = 0; k < cands.size() && s == SRE_OK; ++k) {
+            s = time_cfg(cands[k], xe1, &ms);
+            screen.emplace_back(ms, k);
+        }
+    }
     double best_ms = 1e30;
     sre::LargeCfg best_c = base;
-    sre_status_t s = SRE_OK;
-    for (sre::LargeCfg &c : cands) {
-        float ms = 0.f, ms_min = 1e30f;
-        for (int rep = 0; rep < 3 && s == SRE_OK; ++rep) {
-            cudaEventRecord(e0, st);
-            s = enqueue_plan_cfg(p, p->tune_state, N, xb, xe, st, nullptr, nullptr, &c);
-            cudaEventRecord(e1, st);
-            if (s != SRE_OK) break;
-            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
-                s = cuda_fail(e);
-                break;
+    if (s == SRE_OK) {
+        std::sort(screen.begin(), screen.end());
+        const uint64_t xe2 = std::min<uint64_t>(xb + 4 * n, d);
+        const size_t keep = std::min<size_t>(screen.size(), 8);
+        for (size_t k = 0; k < keep && s == SRE_OK; ++k) {
+            const sre::LargeCfg &c = cands[screen[k].second];
+            float ms = 0.f, ms_min = 1e30f;
+            for (int rep = 0; rep < 2 && s == SRE_OK; ++rep) {
+                s = time_cfg(c, xe2, &ms);
+                ms_min = std::min(ms_min, ms);
             }
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) ms_min = std::min(ms_min, ms);
-        }
-        if (s != SRE_OK) break;
-        if (ms_min < best_ms) {
-            best_ms = ms_min;
-            best_c = c;
+            // reported per the screening slice's length
+            const double per = (double)ms_min * (double)(xe - xb) / (double)(xe2 - xb);
+            if (s == SRE_OK && per < best_ms) {
+                best_ms = per;
+                best_c = c;
+            }
         }
     }
     cudaEventDestroy(e0);

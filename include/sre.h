@@ -118,7 +118,13 @@ SRE_API sre_status_t sre_plan_get_mode(sre_plan_t plan, sre_mode_t *mode);
  * lag: how many chunks pass 2 trails pass 1 (1 <= lag < ring_slots);
  * pass2_tiles_log: log2 of the 2^12-entry tiles per pass-2 work item;
  * pass1_blocks_log: log2 of the consecutive 2^12-entry blocks of t per
- * pass-1 work item.
+ * pass-1 work item;
+ * pass1_staged (0/1): pass 1 takes each block and its partner block by bulk
+ * copy into shared memory (FP32 CUDA-core path, x_batch_log = 0 and a
+ * 16-byte aligned state; otherwise, or with 0, per-thread loads);
+ * pass2_staged (0/1): pass 2 takes its tiles by 2-D tensor-memory-accelerator
+ * copies into shared memory (FP32, 17 <= N <= 21; otherwise, or with 0,
+ * per-thread loads).
  * A value of -1 keeps the library's choice for that field; all -1 restores
  * the defaults.  The scratch ring must fit the plan's allocation
  * (SRE_EINVAL otherwise).  Applies to the halved shifts (x >= 4096).
@@ -129,6 +135,8 @@ typedef struct {
     int lag;
     int pass2_tiles_log;
     int pass1_blocks_log;
+    int pass1_staged;
+    int pass2_staged;
 } sre_tuning_t;
 SRE_API sre_status_t sre_plan_set_tuning(sre_plan_t plan, const sre_tuning_t *tuning);
 SRE_API sre_status_t sre_plan_get_tuning(sre_plan_t plan, int N, sre_tuning_t *tuning);

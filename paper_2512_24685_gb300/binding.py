@@ -55,7 +55,8 @@ class SreError(RuntimeError):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("x_batch_log", ctypes.c_int), ("ring_slots", ctypes.c_int), ("lag", ctypes.c_int),
-                ("pass2_tiles_log", ctypes.c_int), ("pass1_blocks_log", ctypes.c_int)]
+                ("pass2_tiles_log", ctypes.c_int), ("pass1_blocks_log", ctypes.c_int),
+                ("pass1_staged", ctypes.c_int), ("pass2_staged", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -211,10 +212,10 @@ class Plan:
         return ms.value, (name.value or b"").decode()
 
     def set_tuning(self, x_batch_log=-1, ring_slots=-1, lag=-1, pass2_tiles_log=-1,
-                   pass1_blocks_log=-1):
+                   pass1_blocks_log=-1, pass1_staged=-1, pass2_staged=-1):
         """sre_plan_set_tuning: override two-pass fields (-1 = library choice)."""
         t = Tuning(int(x_batch_log), int(ring_slots), int(lag), int(pass2_tiles_log),
-                   int(pass1_blocks_log))
+                   int(pass1_blocks_log), int(pass1_staged), int(pass2_staged))
         _check(load_library().sre_plan_set_tuning(self._h, ctypes.byref(t)), "sre_plan_set_tuning")
 
     def get_tuning(self, N: int) -> dict:

@@ -3,9 +3,11 @@
     python -m paper_2512_24685_gb300.cli m2 --N 20 [--family haar] [--seed S] [--mode fp32]
     python -m paper_2512_24685_gb300.cli range --N 20 --x-begin B --count C [--per-x]
 
-Both take --tuning C_LOG,R,D,G2,B1 (the two-pass kernel's chunk size, ring
-slots, lag, pass-2 tiles and pass-1 blocks per item, logs base 2 where
-named so; -1 keeps the default) or --autotune (sre_plan_autotune first).
+Both take --tuning C_LOG,R,D,G2,B1[,S1,S2] (the two-pass kernel's chunk
+size, ring slots, lag, pass-2 tiles and pass-1 blocks per item, logs base 2
+where named so, and whether pass 1 / pass 2 take their data by bulk copy
+into shared memory; -1 keeps the default) or --autotune
+(sre_plan_autotune first).
 
 `m2` evaluates M2 of one generated state; `range` evaluates the partial sum
 sum_{x in [B, B+C)} sum_z |<psi|X^x Z^z|psi>|^4 through sre_sum4_range (the
@@ -47,7 +49,7 @@ def main(argv=None):
         p.add_argument("--dtype", default="c64", choices=["c64", "c128"])
         p.add_argument("--mode", default=None)
         p.add_argument("--repeat", type=int, default=1)
-        p.add_argument("--tuning", default=None, help="C_LOG,R,D,G2,B1 of the halved-shift launch")
+        p.add_argument("--tuning", default=None, help="C_LOG,R,D,G2,B1[,S1,S2] of the halved-shift launch")
         p.add_argument("--autotune", action="store_true")
         if name == "range":
             p.add_argument("--x-begin", type=int, required=True)

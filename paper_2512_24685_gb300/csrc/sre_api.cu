@@ -45,7 +45,7 @@ struct sre_plan_s {
     sre::BatchedContext *batched = nullptr;
     bool profiling = false;
     unsigned long long extra_launches = 0;  // launches of workspaces that were freed
-    sre_tuning_t user = {-1, -1, -1, -1, -1};           // sre_plan_set_tuning
+    sre_tuning_t user = {-1, -1, -1, -1, -1, -1, -1};           // sre_plan_set_tuning
     sre::LargeCfg tuned[SRE_MAX_QUBITS + 1];        // sre_plan_autotune results
     bool has_tuned[SRE_MAX_QUBITS + 1] = {};
     void *tune_state = nullptr;                     // synthetic state for autotuning
@@ -218,6 +218,8 @@ static sre::LargeCfg plan_cfg(sre_plan_t p, int N) {
     if (p->user.lag >= 0) c.D = p->user.lag;
     if (p->user.pass2_tiles_log >= 0) c.G2_log = p->user.pass2_tiles_log;
     if (p->user.pass1_blocks_log >= 0) c.B1_log = p->user.pass1_blocks_log;
+    if (p->user.pass1_staged >= 0) c.stage1 = p->user.pass1_staged;
+    if (p->user.pass2_staged >= 0) c.stage2 = p->user.pass2_staged;
     c.G2_log = std::min(c.G2_log, N - sre::kTileBits - 1);
     c.B1_log = std::min(c.B1_log, N - sre::kTileBits - 1);
     return c;
@@ -255,7 +257,8 @@ static sre_status_t enqueue_plan_cfg(sre_plan_t p, const void *d_state, int N, u
 sre_status_t sre_plan_set_tuning(sre_plan_t p, const sre_tuning_t *t) {
     if (!p || !t) return SRE_EINVAL;
     if (t->x_batch_log > 3 || t->ring_slots > sre::kMaxRing || (t->ring_slots >= 0 && t->ring_slots < 2) ||
-        (t->lag >= 0 && t->lag < 1) || t->pass2_tiles_log > 12 || t->pass1_blocks_log > 12)
+        (t->lag >= 0 && t->lag < 1) || t->pass2_tiles_log > 12 || t->pass1_blocks_log > 12 ||
+        t->pass1_staged > 1 || t->pass2_staged > 1)
         return SRE_EINVAL;
     p->user = *t;
     return SRE_OK;
@@ -264,7 +267,7 @@ sre_status_t sre_plan_set_tuning(sre_plan_t p, const sre_tuning_t *t) {
 sre_status_t sre_plan_get_tuning(sre_plan_t p, int N, sre_tuning_t *t) {
     if (!p || !t || N < 1 || N > p->N) return SRE_EINVAL;
     if (N <= sre::kTileBits) {
-        *t = {-1, -1, -1, -1, -1};
+        *t = {-1, -1, -1, -1, -1, -1, -1};
         return SRE_OK;
     }
     const sre::LargeCfg c = plan_cfg(p, N);
@@ -273,6 +276,8 @@ sre_status_t sre_plan_get_tuning(sre_plan_t p, int N, sre_tuning_t *t) {
     t->lag = c.D;
     t->pass2_tiles_log = c.G2_log;
     t->pass1_blocks_log = c.B1_log;
+    t->pass1_staged = c.stage1;
+    t->pass2_staged = c.stage2;
     return SRE_OK;
 }
 
@@ -289,20 +294,23 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
     if ((e = sre::enqueue_fill_synthetic(p->tune_state, N, p->dtype, st)) != cudaSuccess) return cuda_fail(e);
     // candidates: chunk size C, pass-2 tiles per item G2, pass-1 blocks per
     // item B1, and a lag D of 1-3 times the lag steps the grid covers at
-    // once (one lag step claims the P1 + P2 items of a chunk)
+    // once (one lag step claims the P1 + P2 items of a chunk) or the largest
+    // ring 2 D + 1 the scratch holds
     const int eb = elem_bytes_for_mode(p->mode);
     const sre::LargeCfg base = sre::choose_large_cfg(p->dev, N, eb, 1);
     const int h2 = N - sre::kTileBits - 1;
     std::vector<sre::LargeCfg> cands;
     auto add = [&](const sre::LargeCfg &c) {
         for (const sre::LargeCfg &o : cands)
-            if (o.C_log == c.C_log && o.G2_log == c.G2_log && o.B1_log == c.B1_log && o.D == c.D) return;
+            if (o.C_log == c.C_log && o.G2_log == c.G2_log && o.B1_log == c.B1_log && o.D == c.D &&
+                o.stage1 == c.stage1 && o.stage2 == c.stage2)
+                return;
         if (sre::large_cfg_fits(p->ws, c, N, 1)) cands.push_back(c);
     };
     for (int C_log = 0; C_log <= 3; ++C_log)
         for (int g = 0; g <= 3; ++g)
             for (int b = 2; b <= 3; ++b)
-                for (int dm = 1; dm <= 3; ++dm) {
+                for (int dm = 0; dm <= 3; ++dm) {
                     sre::LargeCfg c = base;
                     c.C_log = C_log;
                     c.G2_log = std::min(h2, C_log + g);
@@ -310,14 +318,22 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
                     const int P1 = 1 << (h2 - c.B1_log);
                     const int P2 = (1 << C_log) << (h2 - c.G2_log);
                     const int steps = std::max(1, (base.grid + P1 + P2 - 1) / (P1 + P2));
-                    c.D = std::min(dm * steps + 1, sre::kMaxRing / 2 - 1);
                     // ring of 2 D + 1 chunks, or as many as the scratch holds
                     // (at least D + 2)
                     const size_t per_chunk = ((size_t)eb << (N - 1)) << C_log;
                     const int r_fit = (int)std::min<size_t>(p->ws.scratch_bytes / per_chunk, sre::kMaxRing);
+                    c.D = std::min(dm > 0 ? dm * steps + 1 : (r_fit - 1) / 2, sre::kMaxRing / 2 - 1);
+                    if (c.D < 1) continue;
                     c.R = std::min(2 * c.D + 1, r_fit);
                     if (c.R < c.D + 2) continue;
-                    add(c);
+                    // both copy paths where they apply
+                    const bool tma = eb == 8 && h2 >= 5 && h2 <= 8;
+                    for (int s1 = (C_log == 0 && eb == 8) ? 0 : 1; s1 <= 1; ++s1)
+                        for (int s2 = tma ? 0 : 1; s2 <= 1; ++s2) {
+                            c.stage1 = s1;
+                            c.stage2 = s2;
+                            add(c);
+                        }
                 }
     if (cands.empty()) return SRE_OK;
     // a slice of halved shifts worth ~2^34 entries of work
@@ -331,8 +347,8 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
         cudaEventDestroy(e0);
         return cuda_fail(e);
     }
-    // Two rounds: every candidate once on twice the slice (after one warm-up
-    // launch), then the fastest eight twice on four times the slice, which
+    // Two rounds: every candidate once on the slice (after one warm-up
+    // launch), then the fastest twelve twice on four times the slice, which
     // ranks the candidates in steady state.
     sre_status_t s = SRE_OK;
     auto time_cfg = [&](sre::LargeCfg c, uint64_t x_end, float *ms) -> sre_status_t {
@@ -347,7 +363,7 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
     std::vector<std::pair<float, size_t>> screen;
     {
         float ms = 0.f;
-        const uint64_t xe1 = std::min<uint64_t>(xb + 2 * n, d);
+        const uint64_t xe1 = xe;
         s = time_cfg(cands[0], xe, &ms);  // warm-up
         for (size_t k = 0; k < cands.size() && s == SRE_OK; ++k) {
             s = time_cfg(cands[k], xe1, &ms);
@@ -359,7 +375,7 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
     if (s == SRE_OK) {
         std::sort(screen.begin(), screen.end());
         const uint64_t xe2 = std::min<uint64_t>(xb + 4 * n, d);
-        const size_t keep = std::min<size_t>(screen.size(), 8);
+        const size_t keep = std::min<size_t>(screen.size(), 12);
         for (size_t k = 0; k < keep && s == SRE_OK; ++k) {
             const sre::LargeCfg &c = cands[screen[k].second];
             float ms = 0.f, ms_min = 1e30f;
@@ -386,6 +402,8 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
         best->lag = best_c.D;
         best->pass2_tiles_log = best_c.G2_log;
         best->pass1_blocks_log = best_c.B1_log;
+        best->pass1_staged = best_c.stage1;
+        best->pass2_staged = best_c.stage2;
     }
     if (ms_out) *ms_out = best_ms;
     return SRE_OK;

@@ -37,6 +37,8 @@ struct LargeCfg {
     int G2_log;  // log2 tiles per pass-2 work item
     int B1_log;  // log2 consecutive blocks per pass-1 work item
     int grid;    // persistent CTAs
+    int stage1 = 1;  // pass 1 by bulk copy where available (C = 1, FP32, aligned)
+    int stage2 = 1;  // pass 2 by TMA tile copies where available (FP32, 5 <= h2 <= 8)
 };
 
 // Everything one evaluation needs on the device (owned by a plan or a

@@ -250,6 +250,8 @@ LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half
     c.G2_log = std::min(C_log, h2);
     // pass 2 staged through TMA (FP32, 5 <= h2 <= 8) overlaps the copy of
     // tile g + 2 with tile g: give each item four tiles or more
+    c.stage1 = 1;
+    c.stage2 = 1;
     if (elem_bytes == 8 && h2 >= 5 && h2 <= 8) c.G2_log = std::min(C_log + 2, h2);
     c.B1_log = 0;
     return c;
@@ -458,6 +460,8 @@ static cudaError_t make_large_args(LargeArgs *a, const Workspace &ws, const Devi
     A.D = (int)std::max<long long>(1, std::min<long long>(std::min(c.D, c.R - 1), A.n_chunks));
     if (A.R < 2) return cudaErrorInvalidValue;
     A.B1_log = std::max(0, std::min(c.B1_log, A.h2));
+    A.stage1 = c.stage1;
+    A.stage2 = c.stage2;
     A.P1 = 1 << (A.h2 - A.B1_log);
     A.P2 = (1 << c.C_log) << (A.h2 - A.G2_log);
     A.n_items = A.n_chunks * (long long)(A.P1 + A.P2);
@@ -768,6 +772,8 @@ static cudaError_t enqueue_batch_class_t(const Workspace &ws, const DeviceInfo &
         A.R = c.R;
         A.G2_log = std::min(c.G2_log, A.h2);
         A.B1_log = std::max(0, std::min(c.B1_log, A.h2));
+        A.stage1 = c.stage1;
+        A.stage2 = c.stage2;
         A.n_chunks = cps * L.S;
         A.D = (int)std::max<long long>(1, std::min<long long>(std::min(c.D, c.R - 1), A.n_chunks));
         A.P1 = 1 << (A.h2 - A.B1_log);

@@ -58,6 +58,7 @@ struct LargeArgs {
     uint64_t x_begin, x_end;   // evaluated shift range
     uint64_t x0;               // x_begin rounded down to a chunk boundary
     int C_log, R, D, G2_log, B1_log;
+    int stage1, stage2;        // staged copy paths enabled (LargeCfg)
     long long n_chunks;
     int P1, P2;                // items per chunk in pass 1 / pass 2
     long long n_items;
@@ -84,27 +85,6 @@ static __device__ bool wait_counter(const unsigned *p, unsigned target, int *sta
     }
     atomicCAS(status, 0, (int)SRE_ETIMEDOUT);
     return false;
-}
-
-// Store a pass-1 block (round-0 layout: thread tid holds z_l = 16 tid + i)
-// to its 4096 scratch entries.  Pass 2 transforms across blocks entry by
-// entry and sums over z, so any z order shared by all blocks is valid; the
-// order used makes every warp store one contiguous run: FP32 stores the pair
-// (2j, 2j + 1) as one 16-byte word at entries 512 j + 2 tid (+1), FP64 entry
-// i at 256 i + tid.
-template <typename R>
-__device__ __forceinline__ void store_block(v2_t<R> *blk, const cx_t<R> (&v)[16], int tid) {
-    if constexpr (sizeof(R) == 4) {
-        float4 *o = reinterpret_cast<float4 *>(blk) + tid;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float2 lo = Cx<float>::to(v[2 * j]), hi = Cx<float>::to(v[2 * j + 1]);
-            __stcg(o + (j << 8), make_float4(lo.x, lo.y, hi.x, hi.y));
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) __stcg(blk + tid + (i << 8), Cx<R>::to(v[i]));
-    }
 }
 
 // item -> (chunk, index within its pass, pass) for the lagged order.
@@ -165,39 +145,6 @@ __host__ __device__ constexpr size_t large_smem_bytes(size_t tc_extra) {
 // Host: encode LargeArgs::tmap for the launch's scratch ring.
 cudaError_t encode_p2_tmap(LargeArgs &a);
 
-// What an item is: its chunk, index within its pass, pass, ring slot, state
-// and first shift (chunk c of a batch class belongs to state c / chunks per
-// state).
-struct ItemDesc {
-    long long c;
-    int r;
-    bool pass1;
-    int slot;
-    const void *psi;
-    uint64_t xc;
-};
-
-__device__ __forceinline__ ItemDesc describe_item(const LargeArgs &a, long long item) {
-    ItemDesc d;
-    decode_item(a, item, d.c, d.r, d.pass1);
-    d.slot = (int)(d.c % a.R);
-    long long cl = d.c;
-    d.psi = a.psi;
-    if (a.psis) {
-        const long long sidx = d.c / a.chunks_per_state;
-        cl = d.c - sidx * a.chunks_per_state;
-        d.psi = a.psis[sidx];
-    }
-    d.xc = a.x0 + ((uint64_t)cl << a.C_log);
-    return d;
-}
-
-// t_h of the pass-1 block t'_h: a zero inserted at bit jh (halved shifts).
-template <bool HALF>
-__device__ __forceinline__ int block_th(int tp, int jh) {
-    return HALF ? (((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1))) : tp;
-}
-
 template <typename R, int H2, bool HALF, int TC = kTcNone>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(const __grid_constant__ LargeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -207,17 +154,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
     unsigned char *sbase = smem_raw;
     if constexpr (kTma) sbase += (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     V *bufB = reinterpret_cast<V *>(sbase);  // round 1 -> 2 moves, alternating with
-    V *bufC = bufB + kTileSlots;             //   bufC from tile to tile; copy stages
+    V *bufC = bufB + kTileSlots;             //   bufC from tile to tile; pass-2 stages
     V *bufA = bufC + kTileSlots;             // warp-local moves
     __shared__ long long s_next[2];
     __shared__ int s_stop[2];
-    // copy barriers: [0], [1] the pass-2 tile stages (kTma), [2] the pass-1
+    // stage barriers: [0], [1] the pass-2 tile stages (kTma), [2] the pass-1
     // block pair (kStage1)
     __shared__ __align__(8) uint64_t s_mbar[3];
     unsigned tcount = 0;  // tiles that used a round 1 -> 2 move (uniform)
     uint32_t sphase = 0;  // parity of the next completion of each barrier
     uint32_t slost = 0;   // barriers whose completion wait expired
-    int pre = 0;          // thread 0: copies of the next item already issued (1 pass 1, 2 pass 2)
 
     // tensor-core stage (TC != kTcNone, FP32 only): H_16 operand, mbarrier
     // and TMEM after the three relayout buffers
@@ -241,75 +187,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
     const int tid = threadIdx.x;
     const int lgx = a.N - (HALF ? 1 : 0);        // log2 scratch entries per shift
     const int C = 1 << a.C_log;
+    const V *psi0 = reinterpret_cast<const V *>(a.psi);
     V *scratch = reinterpret_cast<V *>(a.scratch);
     constexpr int zsub_bits = kTileBits - H2;     // z entries per block in pass 2
     const int ipx_log = H2 - a.G2_log;            // pass-2 items per shift (log2)
-    const int ntiles = 1 << a.G2_log;             // pass-2 tiles per item
 
     const int warp = tid >> 5, lane = tid & 31;
     constexpr int kWarps = kThreads / 32;
-
-    // ---- copy issue (thread 0 only)
-    // pass 1, staged: the block pair kb of item d into the two stages
-    auto staged1 = [&](const ItemDesc &d) -> bool {
-        return kStage1 && C == 1 && ((uintptr_t)d.psi & 15) == 0 && d.xc >= a.x_begin && d.xc < a.x_end;
-    };
-    auto issue_pair = [&](const ItemDesc &d, int kb) {
-        const uint64_t xh = d.xc >> kTileBits;
-        const int jh = HALF ? (63 - __clzll((long long)d.xc)) - kTileBits : 0;
-        const int th = block_th<HALF>((d.r << a.B1_log) + kb, jh);
-        const V *p = reinterpret_cast<const V *>(d.psi);
-        const uint32_t mb = smem_u32(&s_mbar[2]);
-        mbar_arrive_expect_tx(mb, 2u * kStageBytes);
-        bulk_load(smem_u32(bufB), p + ((uint64_t)th << kTileBits), kStageBytes, mb);
-        bulk_load(smem_u32(bufC), p + (((uint64_t)th ^ xh) << kTileBits), kStageBytes, mb);
-    };
-    // pass 2, staged: tile g of item d into stage st (ok = false: no copy,
-    // the waiters are released on garbage)
-    auto live2 = [&](const ItemDesc &d) -> bool {
-        const uint64_t x = d.xc + (uint64_t)(d.r >> ipx_log);
-        return x >= a.x_begin && x < a.x_end;
-    };
-    auto issue_tile = [&](const ItemDesc &d, int g, int st, bool ok) {
-        const uint32_t mb = smem_u32(&s_mbar[st]);
-        if (!ok) {
-            mbar_arrive(mb);
-            return;
-        }
-        const int xl = d.r >> ipx_log;
-        const int zb0 = (d.r & ((1 << ipx_log) - 1)) << a.G2_log;
-        const int y = (int)(((size_t)d.slot * C + xl) << H2);
-        const uint32_t dst = smem_u32(st ? (void *)bufC : (void *)bufB);
-        const int x0 = (zb0 + g) << (kTileBits - H2 + 1);  // FP32 column
-        mbar_arrive_expect_tx(mb, (uint32_t)kStageBytes);
-#pragma unroll
-        for (int b = 0; b < (1 << (8 - (H2 < 8 ? H2 : 8))); ++b)
-            tma_load_2d(dst + (uint32_t)b * (128u << H2), &a.tmap, x0 + 32 * b, y, mb);
-    };
-    // With both stages free at the end of an item: start the next item's
-    // first copies when they need no wait (a staged pass-1 item, or a pass-2
-    // item whose chunk has finished pass 1).  The generic-proxy accesses to
-    // the stages (and the acquired pass-1 stores) precede the copies through
-    // the proxy fence.
-    auto preissue = [&](long long nxt) {
-        if (nxt >= a.n_items || *(volatile int *)a.status != 0) return;
-        const ItemDesc d = describe_item(a, nxt);
-        if (d.pass1) {
-            if (staged1(d)) {
-                fence_proxy_async();
-                issue_pair(d, 0);
-                pre = 1;
-            }
-        } else if constexpr (kTma) {
-            if (live2(d) && ld_acquire_u32(a.done1 + d.c) >= (unsigned)(a.P1 * kWarps)) {
-                fence_proxy_async();
-                issue_tile(d, 0, 0, true);
-                if (ntiles > 1) issue_tile(d, 1, 1, true);
-                pre = 2;
-            }
-        }
-    };
-
     // Item claims are prefetched one item ahead through a two-entry slot;
     // s_stop carries a recorded error so that the whole CTA stops together.
     if (tid == 0) {
@@ -325,15 +209,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
         if (item >= a.n_items || s_stop[par]) break;
         long long next = 0;
         if (tid == 0) next = (long long)atomicAdd(a.work, 1ull);
-        const ItemDesc d = describe_item(a, item);
-        const long long c = d.c;
-        const int r = d.r;
-        const int slot = d.slot;
-        const V *psi = reinterpret_cast<const V *>(d.psi);
-        const uint64_t xc = d.xc;
+        long long c;
+        int r;
+        bool pass1;
+        decode_item(a, item, c, r, pass1);
+        const int slot = (int)(c % a.R);
+        // batch class: chunk c belongs to state c / chunks_per_state
+        long long cl = c;
+        const V *psi = psi0;
+        if (a.psis) {
+            const long long sidx = c / a.chunks_per_state;
+            cl = c - sidx * a.chunks_per_state;
+            psi = reinterpret_cast<const V *>(a.psis[sidx]);
+        }
+        const uint64_t xc = a.x0 + ((uint64_t)cl << a.C_log);
         V *slot_base = scratch + (size_t)slot * ((size_t)C << lgx);
 
-        if (d.pass1) {
+        if (pass1) {
             // ---------------- pass 1: blocks t'_h in [r 2^B1, (r+1) 2^B1) of
             // every shift in the chunk.  Each warp waits for the ring slot
             // itself (an expired wait records SRE_ETIMEDOUT; the CTA then
@@ -347,29 +239,33 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
             const uint64_t xh = xc >> kTileBits;
             const int xl0 = (int)(xc & (kTile - 1));
             const int jh = HALF ? (63 - __clzll((long long)xc)) - kTileBits : 0;
-            if (kStage1 && C == 1 && ((uintptr_t)psi & 15) == 0) {
+            if (kStage1 && a.stage1 && C == 1 && ((uintptr_t)psi & 15) == 0) {
                 // One shift per chunk and a 16-byte aligned state: the block
                 // t_h and its partner t_h ^ x_h arrive by two 32 KB bulk copies
                 // in the two stage buffers.  The products overwrite the own
                 // block in place (each thread rewrites only the entries it
                 // read) and that buffer serves the CTA-wide move; once it has
-                // been read back the next pair's copies are issued (the next
-                // item's, after the last pair), so they overlap the rest of
-                // the tile.
-                if (staged1(d)) {
+                // been read back the next pair's copies are issued, so they
+                // overlap the rest of the tile.
+                if (xc >= a.x_begin && xc < a.x_end) {
                     const int nb = 1 << a.B1_log;
                     const uint32_t mb = smem_u32(&s_mbar[2]);
                     V *own = bufB;
                     const V *par = bufC;
+                    auto issue_pair = [&](int kb) {
+                        const int tp = (r << a.B1_log) + kb;
+                        const int th = HALF ? (((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1))) : tp;
+                        mbar_arrive_expect_tx(mb, 2u * kStageBytes);
+                        bulk_load(smem_u32(own), psi + ((uint64_t)th << kTileBits), kStageBytes, mb);
+                        bulk_load(smem_u32(par), psi + (((uint64_t)th ^ xh) << kTileBits), kStageBytes, mb);
+                    };
                     if (tid == 0) {
-                        if (pre != 1) {
-                            fence_proxy_async();
-                            issue_pair(d, 0);
-                        }
-                        pre = 0;
+                        fence_proxy_async();
+                        issue_pair(0);
                     }
-                    const int q = xl0 >> 8;
-                    const int pl = tid ^ (xl0 & 255);
+                    const int xlow = xl0;
+                    const int q = xlow >> 8;
+                    const int pl = tid ^ (xlow & 255);
                     for (int kb = 0; kb < nb; ++kb) {
                         const int tp = (r << a.B1_log) + kb;
                         if (!mbar_wait_bounded(mb, (sphase >> 2) & 1u, a.wait_ns)) {
@@ -391,24 +287,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] = Cx<R>::from(own[elem<1>(tid, i)]);
                         __syncthreads();  // both stage buffers are free
-                        if (tid == 0) {
-                            if (kb + 1 < nb) {
-                                fence_proxy_async();
-                                issue_pair(d, kb + 1);
-                            } else {
-                                preissue(next);
-                            }
+                        if (tid == 0 && kb + 1 < nb) {
+                            fence_proxy_async();
+                            issue_pair(kb + 1);
                         }
                         reg_stages<1, 12, R>(v);
                         relayout<1, 0, true, R>(v, bufA, tid);
                         reg_stages<0, 12, R>(v);
-                        store_block<R>(slot_base + ((size_t)tp << kTileBits), v, tid);
+                        V *o = slot_base + ((size_t)tp << kTileBits) + tid;
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) __stcg(o + (i << 8), Cx<R>::to(v[i]));
                     }
                 }
             } else
             for (int kb = 0; kb < (1 << a.B1_log); ++kb) {
                 const int tp = (r << a.B1_log) + kb;
-                const int th = block_th<HALF>(tp, jh);
+                const int th = HALF ? (((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1))) : tp;
                 // Round-2 layout: thread tid holds t_l = i << 8 | tid of block th
                 // (own factors phi_t in registers); its partners t ^ x are
                 // t_l ^ xlow of block th ^ x_h, read coalesced (each warp load
@@ -452,7 +346,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
                     } else {
                         tile_fwht12_rev<R>(v, bufA, bB, tid);
                     }
-                    store_block<R>(slot_base + ((size_t)xl << lgx) + ((size_t)tp << kTileBits), v, tid);
+                    // output in round-0 layout (z_l = 16 tid + i) stored at the
+                    // bit-permuted position i << 8 | tid: coalesced stores; pass 2
+                    // only sums over z, so the order of z inside a block is free
+                    V *o = slot_base + ((size_t)xl << lgx) + ((size_t)tp << kTileBits) + tid;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) __stcg(o + (i << 8), Cx<R>::to(v[i]));
                 }
             }
             // per-warp completion: every lane's stores are fenced, then one arrival
@@ -461,30 +360,41 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
             if (lane == 0) atomicAdd(a.done1 + c, 1u);
         } else {
             // ---------------- pass 2: 2^G2 z-blocks of one shift; per-warp
-            // partial sums and per-warp completion
+            // wait, per-warp partial sums and per-warp completion
             const int j = r;
             const int xl = j >> ipx_log;
             const int zb0 = (j & ((1 << ipx_log) - 1)) << a.G2_log;
             const uint64_t x = xc + (uint64_t)xl;
-            const bool live = x >= a.x_begin && x < a.x_end;
             double acc = 0.0;
+            const bool staged2 = kTma && a.stage2;
             if constexpr (kTma) {
                 // One thread waits for the chunk's pass 1 and keeps two TMA
-                // tile copies in flight (the first two possibly issued by the
-                // previous item); every thread waits on the stage's mbarrier,
-                // reads the tile in layout A and transforms it.
-                if (live) {
+                // tile copies in flight; every thread waits on the stage's
+                // mbarrier, reads the tile in layout A and transforms it.
+                if (staged2 && x >= a.x_begin && x < a.x_end) {
+                    const int ntiles = 1 << a.G2_log;
+                    const int y = (int)(((size_t)slot * C + xl) << H2);
                     int ok = 1;
-                    if (tid == 0) {
-                        if (pre != 2) {
-                            ok = wait_counter(a.done1 + c, (unsigned)(a.P1 * kWarps), a.status, a.wait_ns);
-                            // pass-1 stores (acquired above) and this CTA's earlier
-                            // shared-memory accesses before the async-proxy copies
-                            fence_proxy_async();
-                            issue_tile(d, 0, 0, ok);
-                            if (ntiles > 1) issue_tile(d, 1, 1, ok);
+                    auto issue = [&](int g, int st) {
+                        const uint32_t mb = smem_u32(&s_mbar[st]);
+                        if (!ok) {
+                            mbar_arrive(mb);  // no copy: release the waiters on garbage
+                            return;
                         }
-                        pre = 0;
+                        const uint32_t dst = smem_u32(st ? (void *)bufC : (void *)bufB);
+                        const int x0 = (zb0 + g) << (kTileBits - H2 + 1);  // FP32 column
+                        mbar_arrive_expect_tx(mb, (uint32_t)kStageBytes);
+#pragma unroll
+                        for (int b = 0; b < (1 << (8 - H2)); ++b)
+                            tma_load_2d(dst + (uint32_t)b * (128u << H2), &a.tmap, x0 + 32 * b, y, mb);
+                    };
+                    if (tid == 0) {
+                        ok = wait_counter(a.done1 + c, (unsigned)(a.P1 * kWarps), a.status, a.wait_ns);
+                        // pass-1 stores (acquired above) and this CTA's earlier
+                        // shared-memory accesses before the async-proxy copies
+                        fence_proxy_async();
+                        issue(0, 0);
+                        if (ntiles > 1) issue(1, 1);
                     }
                     const P2Lane pl = p2_lane<H2>(lane, warp);
                     for (int gb = 0; gb < ntiles; ++gb) {
@@ -494,30 +404,26 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
                             if (lane == 0) atomicCAS(a.status, 0, (int)SRE_ETIMEDOUT);
                         }
                         sphase ^= 1u << st;
-                        cx_t<float> v[16];
-                        p2_read<H2>(reinterpret_cast<const unsigned char *>(st ? bufC : bufB), pl, v);
-                        if (gb + 2 < ntiles || gb + 1 == ntiles) {
-                            __syncthreads();  // every thread has read stage st (the last: both stages)
+                        const unsigned char *stage = reinterpret_cast<const unsigned char *>(st ? bufC : bufB);
+                        const float s = p2_tile<H2, HALF>(stage, reinterpret_cast<float2 *>(bufA), pl);
+                        acc += (HALF ? 16.0 : 1.0) * (double)s;
+                        if (gb + 2 < ntiles) {
+                            __syncthreads();  // every thread has read stage st
                             if (tid == 0) {
-                                if (gb + 2 < ntiles) {
-                                    fence_proxy_async();
-                                    issue_tile(d, gb + 2, st, ok);
-                                } else {
-                                    preissue(next);
-                                }
+                                fence_proxy_async();
+                                issue(gb + 2, st);
                             }
                         }
-                        const float s = p2_finish<H2, HALF>(v, reinterpret_cast<float2 *>(bufA), pl);
-                        acc += (HALF ? 16.0 : 1.0) * (double)s;
                     }
                 }
-            } else {
+            }
+            if (!staged2) {
             if (lane == 0) wait_counter(a.done1 + c, (unsigned)(a.P1 * kWarps), a.status, a.wait_ns);
             __syncwarp();
             __threadfence();
-            if (live) {
+            if (x >= a.x_begin && x < a.x_end) {
                 const V *xb = slot_base + ((size_t)xl << lgx);
-                for (int gb = 0; gb < ntiles; ++gb) {
+                for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
                     const int zb = zb0 + gb;
                     cx_t<R> v[16];
 #pragma unroll
@@ -540,18 +446,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-            // All warps' loads of this item are complete after a barrier (the
-            // staged path's last-tile barrier, else this one): drop the
-            // item's scratch lines from L2 without write-back (dead data; the
-            // next chunk in this slot rewrites them).  The drops precede this
-            // item's arrivals, hence the slot's release.
-            if (!(kTma && live)) __syncthreads();
+            // All warps' loads of this item are complete after this barrier:
+            // drop the item's scratch lines from L2 without write-back (dead
+            // data; the next chunk in this slot rewrites them).  The drops
+            // precede this item's arrivals, hence the slot's release.
+            __syncthreads();
             constexpr int kLineElems = 128 / (int)sizeof(V);
-            if (((1 << zsub_bits) >= kLineElems) && live) {
+            if (((1 << zsub_bits) >= kLineElems) && x >= a.x_begin && x < a.x_end) {
                 const V *xb = slot_base + ((size_t)xl << lgx);
                 constexpr int lines_per_row = ((1 << zsub_bits) >= kLineElems) ? (1 << zsub_bits) / kLineElems : 1;
                 constexpr int lines_per_tile = kTile / kLineElems;
-                for (int gb = 0; gb < ntiles; ++gb) {
+                for (int gb = 0; gb < (1 << a.G2_log); ++gb) {
                     const int zb = zb0 + gb;
                     for (int L = tid; L < lines_per_tile; L += kThreads) {
                         const int row = L / lines_per_row;
@@ -599,15 +504,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
         __syncthreads();
     }
     if constexpr (kTma || kStage1) {
-        if (tid == 0) {
-            // copies issued for an item that did not run (the CTA stopped on
-            // an error): wait for them (bounded) before the CTA ends
-            if (pre == 1) mbar_wait_bounded(smem_u32(&s_mbar[2]), (sphase >> 2) & 1u, a.wait_ns);
-            if (pre == 2) {
-                mbar_wait_bounded(smem_u32(&s_mbar[0]), sphase & 1u, a.wait_ns);
-                if (ntiles > 1) mbar_wait_bounded(smem_u32(&s_mbar[1]), (sphase >> 1) & 1u, a.wait_ns);
-            }
-        }
         // a stage whose completion wait expired may still receive its copy:
         // wait for it once more (bounded) before the CTA's memory is released
         for (int st = 0; st < 3; ++st)

@@ -9,8 +9,7 @@
 // 2^(8 - H2) two-dimensional TMA copies per tile (boxes of 16 columns x 2^H2
 // rows, 128-byte rows, 128-byte swizzle) into a shared-memory stage; two
 // stages alternate, so the copy of tile g + 2 is in flight while tile g is
-// transformed (an item's first two copies may be issued by the item before
-// it, once that one has read its last tile).
+// transformed.
 //
 // Thread layouts over a warp's 512 entries (e9 = 9-bit index: row bits
 // r0..r_{H2-1} low, then the low column bits; the warp index supplies the
@@ -168,24 +167,17 @@ __device__ __forceinline__ P2Lane p2_lane(int lane, int warp) {
     return p;
 }
 
-// Read this thread's 16 entries of a staged tile (layout A).
-template <int H2>
-__device__ __forceinline__ void p2_read(const unsigned char *stage, const P2Lane &p, cx_t<float> (&v)[16]) {
+// Transform one staged tile and return this thread's share of the quartic
+// sum: sum (Re W)^4 + (Im W)^4 (HALF) or sum |W|^4.  xbuf is the warp-local
+// exchange buffer (kTileSlots entries, warp w uses [544 w, 544 w + 544)).
+template <int H2, bool HALF>
+__device__ __forceinline__ float p2_tile(const unsigned char *stage, float2 *xbuf, const P2Lane &p) {
     using L = P2Stage<H2>;
     using T = cx_t<float>;
+    T v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i)
         v[i] = *reinterpret_cast<const T *>(stage + (p.stage ^ L::stage_off(L::e9_regA(i), 0)));
-}
-
-// Transform a tile read by p2_read and return this thread's share of the
-// quartic sum: sum (Re W)^4 + (Im W)^4 (HALF) or sum |W|^4.  xbuf is the
-// warp-local exchange buffer (kTileSlots entries, warp w uses
-// [544 w, 544 w + 544)).
-template <int H2, bool HALF>
-__device__ __forceinline__ float p2_finish(cx_t<float> (&v)[16], float2 *xbuf, const P2Lane &p) {
-    using L = P2Stage<H2>;
-    using T = cx_t<float>;
     reg_stages_mask<L::maskA(), float>(v);
     T *xb = reinterpret_cast<T *>(xbuf);
     __syncwarp();

@@ -174,6 +174,36 @@ def test_staged_and_register_pass1_agree(sre, torch_cuda, N, tuning, xr):
     assert abs(px_a[-1].item() - ref) <= 1e-5 * ref
 
 
+@pytest.mark.parametrize("N,tuning", [
+    (18, (2, 23, 11, 2, 0)),
+    (20, (0, 23, 11, 3, 2)),
+])
+def test_copy_paths_agree(sre, torch_cuda, N, tuning):
+    """Pass-2 tiles by TMA copy or by per-thread loads, and pass-1 blocks by
+    bulk copy or by per-thread loads: every combination gives per-shift sums
+    within FP32 rounding of each other and of the FP64 oracle; the two
+    pass-1 paths alone give identical sums."""
+    torch = torch_cuda
+    psi_np = W.haar_state(N, 91, np.complex64)
+    psi = torch.from_numpy(psi_np).cuda()
+    xr = (4096 - 32, 4096 + 1024)
+    res = {}
+    with sre.Plan(N, "c64") as p:
+        for s1 in (0, 1):
+            for s2 in (0, 1):
+                p.set_tuning(*tuning, s1, s2)
+                _, px = p.sum4_range(psi, xr[0], xr[1], per_x=True)
+                res[(s1, s2)] = px.cpu().numpy()
+    for s2 in (0, 1):
+        assert np.array_equal(res[(0, s2)], res[(1, s2)])
+    ref = res[(0, 0)]
+    assert np.max(np.abs(res[(1, 1)] - ref)) <= 1e-6 * np.max(ref)
+    for x in (xr[0], 4095, 4096, xr[1] - 1):
+        o = oracle.sum4_xorfwht(psi_np, x, x + 1)
+        for v in res.values():
+            assert abs(v[x - xr[0]] - o) <= 1e-5 * o
+
+
 # -------------------------------------------------- full-size (N = 20) checks
 
 def test_n20_full_size_sampled(sre, torch_cuda):

@@ -75,6 +75,13 @@ def _load():
             _dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _dp]
         lib.sre_oracle_m2.restype = ctypes.c_double
         lib.sre_oracle_m2.argtypes = [_dp, ctypes.c_int, ctypes.c_int]
+        lib.sre_oracle_sum_pow_direct.restype = ctypes.c_double
+        lib.sre_oracle_sum_pow_direct.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp]
+        lib.sre_oracle_sum_pow_xorfwht_range.restype = ctypes.c_double
+        lib.sre_oracle_sum_pow_xorfwht_range.argtypes = [
+            _dp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _dp]
+        lib.sre_oracle_malpha.restype = ctypes.c_double
+        lib.sre_oracle_malpha.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.sre_oracle_num_threads.restype = ctypes.c_int
         lib.sre_oracle_set_threads.restype = None
         lib.sre_oracle_set_threads.argtypes = [ctypes.c_int]
@@ -174,3 +181,42 @@ def m2(psi, method: str = "auto") -> float:
         method = "direct" if N <= 6 else "xorfwht"
     code = {"direct": 0, "xorfwht": 1}[method]
     return _load().sre_oracle_m2(_ptr(a), N, code)
+
+
+# ---- general integer Renyi order (Eq. (sre)) ------------------------------
+
+def sum_pow_direct(psi, alpha: int, per_x: bool = False):
+    """O1 for order alpha: S_alpha = sum_{x,z} |<psi|X^x Z^z|psi>|^(2 alpha)
+    from the definition (8^N)."""
+    a, N = _as_c128(psi)
+    px = np.empty(1 << N) if per_x else None
+    s = _load().sre_oracle_sum_pow_direct(_ptr(a), N, int(alpha), _ptr(px) if per_x else None)
+    return (s, px) if per_x else s
+
+
+def sum_pow_xorfwht(psi, alpha: int, x_begin: int = 0, x_end: int | None = None,
+                    per_x: bool = False):
+    """O2 for order alpha: S_alpha by Algorithm 1's loop over shifts
+    [x_begin, x_end) with the exponent 2 alpha."""
+    a, N = _as_c128(psi)
+    d = 1 << N
+    xe = d if x_end is None else min(int(x_end), d)
+    xb = int(x_begin)
+    px = np.empty(max(xe - xb, 0)) if per_x else None
+    s = _load().sre_oracle_sum_pow_xorfwht_range(_ptr(a), N, int(alpha), xb, xe,
+                                                 _ptr(px) if per_x else None)
+    return (s, px) if per_x else s
+
+
+def malpha_from_sum(S: float, n2: float, N: int, alpha: int) -> float:
+    """M_alpha = log2(S_alpha / (d n2^(2 alpha))) / (1 - alpha)."""
+    return float(np.log2(S / (2.0 ** N * n2 ** (2 * alpha))) / (1 - alpha))
+
+
+def malpha(psi, alpha: int, method: str = "auto") -> float:
+    """M_alpha of Eq. (sre) for integer alpha >= 2. method: 'direct' (O1),
+    'xorfwht' (O2) or 'auto' (O1 for N <= 6, O2 above)."""
+    a, N = _as_c128(psi)
+    if method == "auto":
+        method = "direct" if N <= 6 else "xorfwht"
+    return _load().sre_oracle_malpha(_ptr(a), N, int(alpha), 0 if method == "direct" else 1)

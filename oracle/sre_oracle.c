@@ -223,6 +223,96 @@ double sre_oracle_sum4_xorfwht(const double *psi, int N, double *per_x) {
     return sre_oracle_sum4_xorfwht_range(psi, N, 0, (uint64_t)1 << N, per_x);
 }
 
+/* ---- general integer Renyi order (Eq. (sre)) ---------------------------
+ *
+ * Eq. (sre) defines, for Renyi index alpha,
+ *     M_alpha = 1/(1 - alpha) * log2( (1/d) sum_P |<psi|P|psi>|^{2 alpha} )
+ * over the 4^N Pauli strings of a normalised state.  For the stored state
+ * the sum scales as n2^{2 alpha}, so with S_alpha = sum_{x,z} |A_x(z)|^{2 alpha}
+ *     M_alpha = log2( S_alpha / (d * n2^{2 alpha}) ) / (1 - alpha).
+ * alpha = 2 is M2 above.  Only integer alpha >= 2 is taken (the orders the
+ * paper lists as magic monotones), so |A|^{2 alpha} = (|A|^2)^alpha is a plain
+ * product of alpha factors.
+ */
+static double pow_int(double v, int k) {
+    double p = 1.0;
+    for (int i = 0; i < k; ++i) p *= v;
+    return p;
+}
+
+/* O1 for order alpha: every expectation from Eq. (Pauli_expect) summed
+ * directly, then |.|^{2 alpha} summed over all (x, z).  per_x as in O1. */
+double sre_oracle_sum_pow_direct(const double *psi, int N, int alpha, double *per_x) {
+    const uint64_t d = (uint64_t)1 << N;
+    if (alpha < 1) return NAN;
+    double *px = (double *)malloc(sizeof(double) * d);
+    if (!px) return NAN;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t x = 0; x < (int64_t)d; ++x) {
+        ksum_t k = {0.0, 0.0};
+        for (uint64_t z = 0; z < d; ++z) {
+            double re, im;
+            sre_oracle_pauli_expectation(psi, N, (uint64_t)x, z, &re, &im);
+            ksum_add(&k, pow_int(re * re + im * im, alpha));
+        }
+        px[x] = ksum_get(&k);
+    }
+    ksum_t tot = {0.0, 0.0};
+    for (uint64_t x = 0; x < d; ++x) ksum_add(&tot, px[x]);
+    if (per_x) memcpy(per_x, px, sizeof(double) * d);
+    free(px);
+    return ksum_get(&tot);
+}
+
+/* O2 for order alpha: Algorithm 1's loop (product, FWHT per shift) with the
+ * exponent 2 alpha in place of 4 in the per-shift sum.  Range and per_x as in
+ * sre_oracle_sum4_xorfwht_range. */
+double sre_oracle_sum_pow_xorfwht_range(const double *psi, int N, int alpha, uint64_t x_begin,
+                                        uint64_t x_end, double *per_x) {
+    const uint64_t d = (uint64_t)1 << N;
+    if (alpha < 1) return NAN;
+    if (x_end > d) x_end = d;
+    if (x_begin >= x_end) return 0.0;
+    const uint64_t nx = x_end - x_begin;
+    double *px = (double *)malloc(sizeof(double) * nx);
+    if (!px) return NAN;
+    int fail = 0;
+#pragma omp parallel
+    {
+        double *G = (double *)malloc(sizeof(double) * 2 * d);
+        if (!G) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < (int64_t)nx; ++i) {
+            if (!G) continue;
+            sre_oracle_shift_transform(psi, N, x_begin + (uint64_t)i, G);
+            ksum_t k = {0.0, 0.0};
+            for (uint64_t u = 0; u < d; ++u)
+                ksum_add(&k, pow_int(G[2 * u] * G[2 * u] + G[2 * u + 1] * G[2 * u + 1], alpha));
+            px[i] = ksum_get(&k);
+        }
+        free(G);
+    }
+    if (fail) { free(px); return NAN; }
+    ksum_t tot = {0.0, 0.0};
+    for (uint64_t i = 0; i < nx; ++i) ksum_add(&tot, px[i]);
+    if (per_x) memcpy(per_x, px, sizeof(double) * nx);
+    free(px);
+    return ksum_get(&tot);
+}
+
+/* M_alpha of Eq. (sre) for integer alpha >= 2; method 0 = O1, 1 = O2. */
+double sre_oracle_malpha(const double *psi, int N, int alpha, int method) {
+    if (alpha < 2) return NAN;
+    const double n2 = sre_oracle_norm2(psi, N);
+    const double S = method == 0 ? sre_oracle_sum_pow_direct(psi, N, alpha, NULL)
+                                 : sre_oracle_sum_pow_xorfwht_range(psi, N, alpha, 0, (uint64_t)1 << N, NULL);
+    const double d = ldexp(1.0, N);
+    return log2(S / (d * pow_int(n2, 2 * alpha))) / (1.0 - alpha);
+}
+
 /* M2 = -log2(S / (d * n2^4)), Algorithm 1's return value for the state
  * normalised to n2 = 1.  method 0 = O1 (direct), 1 = O2 (XOR-FWHT). */
 double sre_oracle_m2(const double *psi, int N, int method) {

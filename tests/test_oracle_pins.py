@@ -328,3 +328,106 @@ def test_planted_mistakes_are_caught(oracle_mod):
                  per_x(lambda x: np.conj(psi[(t + x) % d]) * psi[t]),
                  per_x(lambda x: np.conj(psi[t ^ x]) * psi[t], signs=False)):
         assert np.max(np.abs(slip - expect)) > 1e-3 * expect.max()
+
+
+# ------------------------------------- general integer Renyi order (Eq. (sre))
+
+ALPHAS = (2, 3, 4, 6)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_sum_pow_matches_hermitian_pauli_group(oracle_mod, N):
+    """S_alpha = sum over the Hermitian Pauli strings {I,X,Y,Z}^N of
+    |psi^H P psi|^(2 alpha), P from explicit 2x2 matrices (Eq. (sre)), equals
+    the oracle's S_alpha by O1 and O2 for every order tested."""
+    psi = rand_state(N, 700 + N, normalise=False)
+    vals = [abs(np.vdot(psi, kron_list(w) @ psi)) for w in itertools.product([PI, PX, PY, PZ], repeat=N)]
+    for a in ALPHAS:
+        ref = sum(v ** (2 * a) for v in vals)
+        assert oracle_mod.sum_pow_direct(psi, a) == pytest.approx(ref, rel=1e-12), a
+        assert oracle_mod.sum_pow_xorfwht(psi, a) == pytest.approx(ref, rel=1e-12), a
+
+
+@pytest.mark.parametrize("N", [3, 6, 8])
+def test_sum_pow_direct_equals_xorfwht(oracle_mod, N):
+    """O1 == O2 per shift for orders 3, 4, 6; at order 2 both equal the
+    M2 routines exactly (same arithmetic)."""
+    psi = rand_state(N, 800 + N, normalise=False)
+    for a in (3, 4, 6):
+        s1, p1 = oracle_mod.sum_pow_direct(psi, a, per_x=True)
+        s2, p2 = oracle_mod.sum_pow_xorfwht(psi, a, per_x=True)
+        assert np.allclose(p1, p2, rtol=1e-11, atol=0), a
+        assert s1 == pytest.approx(s2, rel=1e-12)
+    assert oracle_mod.sum_pow_direct(psi, 2) == oracle_mod.sum4_direct(psi)
+    assert oracle_mod.sum_pow_xorfwht(psi, 2) == oracle_mod.sum4_xorfwht(psi)
+    assert oracle_mod.malpha(psi, 2) == pytest.approx(oracle_mod.m2(psi), abs=1e-13)
+
+
+@pytest.mark.parametrize("N", [1, 3, 6, 9])
+def test_malpha_product_states_closed_form(oracle_mod, N):
+    """Random product states: M_alpha = sum_q log2((1 + x_q^(2a) + y_q^(2a) +
+    z_q^(2a)) / 2) / (1 - a) (single-qubit Paulis I, X, Y, Z have
+    expectations 1, x, y, z; additivity)."""
+    for seed in range(2):
+        psi, bloch = W.product_state(N, 900 + seed)
+        for a in ALPHAS:
+            expect = np.sum(np.log2((1 + np.sum(bloch ** (2 * a), axis=1)) / 2)) / (1 - a)
+            assert oracle_mod.malpha(psi, a) == pytest.approx(expect, abs=1e-12), a
+
+
+def test_malpha_t_state(oracle_mod):
+    """T|+> has Bloch vector (1/sqrt 2, 1/sqrt 2, 0): M_alpha =
+    log2((1 + 2^(1-a)) / 2) / (1 - a); 3 copies give three times that."""
+    s = 1 / math.sqrt(2)
+    t1 = np.diag([1, np.exp(1j * np.pi / 4)]) @ np.array([s, s], dtype=np.complex128)
+    t3 = np.kron(t1, np.kron(t1, t1))
+    for a in ALPHAS:
+        one = math.log2((1 + 2.0 ** (1 - a)) / 2) / (1 - a)
+        assert oracle_mod.malpha(t1, a) == pytest.approx(one, abs=1e-14), a
+        assert oracle_mod.malpha(t3, a) == pytest.approx(3 * one, abs=1e-12), a
+
+
+@pytest.mark.parametrize("N", [2, 5, 8])
+def test_malpha_stabilizer_zero_and_order_monotone(oracle_mod, N):
+    """Faithfulness at every order (stabilizer states: d Pauli expectations
+    of modulus 1, the rest 0, so S_alpha = d); for a generic state M_alpha
+    does not increase with alpha (a Renyi entropy of the distribution
+    <P>^2 / d, shifted by log2 d)."""
+    for seed in range(2):
+        stab = W.stabilizer_state(N, 60 + seed)
+        for a in ALPHAS:
+            assert abs(oracle_mod.malpha(stab, a)) < 1e-12
+    psi = rand_state(N, 950 + N)
+    m = [oracle_mod.malpha(psi, a) for a in (2, 3, 4, 5, 6)]
+    assert all(m[i] >= m[i + 1] - 1e-12 for i in range(len(m) - 1)), m
+
+
+def test_malpha_invariances(oracle_mod):
+    """Clifford invariance, unnormalised input and additivity at order 3."""
+    rng = np.random.default_rng(5)
+    psi = rand_state(5, 17)
+    m = oracle_mod.malpha(psi, 3)
+    phi = psi.copy()
+    for q in range(5):
+        phi = W.apply_1q(phi, 5, q, W._CLIFF1[rng.integers(len(W._CLIFF1))])
+    for q in range(0, 4, 2):
+        phi = W.apply_2q(phi, 5, q, W._CNOT)
+    assert oracle_mod.malpha(phi, 3) == pytest.approx(m, abs=1e-12)
+    assert oracle_mod.malpha(3.7 * psi, 3) == pytest.approx(m, abs=1e-12)
+    a, b = rand_state(2, 21), rand_state(3, 22)
+    assert oracle_mod.malpha(np.kron(b, a), 3) == pytest.approx(
+        oracle_mod.malpha(a, 3) + oracle_mod.malpha(b, 3), abs=1e-12)
+
+
+def test_malpha_planted_exponent_slip_is_caught(oracle_mod):
+    """A plausible slip -- using |A|^alpha instead of |A|^(2 alpha) -- is
+    caught by the product-state closed form at order 3."""
+    psi, bloch = W.product_state(4, 77)
+    expect = np.sum(np.log2((1 + np.sum(bloch ** 6, axis=1)) / 2)) / (1 - 3)
+    n2 = oracle_mod.norm2(psi)
+    table = oracle_mod.pauli_table(psi)
+    wrong = np.sum(np.abs(table) ** 3)
+    wrong_m = oracle_mod.malpha_from_sum(wrong, n2, 4, 3)
+    assert abs(wrong_m - expect) > 1e-3
+    right = np.sum(np.abs(table) ** 6)
+    assert oracle_mod.malpha_from_sum(right, n2, 4, 3) == pytest.approx(expect, abs=1e-12)

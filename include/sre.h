@@ -50,6 +50,7 @@ extern "C" {
 #endif
 
 #define SRE_MAX_QUBITS 24 /* largest N a plan accepts */
+#define SRE_MAX_ORDER 16  /* largest Renyi order alpha of sre_m_alpha */
 
 typedef enum {
     SRE_OK = 0,
@@ -207,6 +208,33 @@ SRE_API sre_status_t sre_m2_host(sre_plan_t plan, const void *h_state, int N, sr
 SRE_API sre_status_t sre_sum4_range(sre_plan_t plan, const void *d_state, int N, uint64_t x_begin,
                             uint64_t x_end, sre_stream_t stream, double *d_out,
                             double *d_per_x);
+
+/*
+ * Stabilizer Renyi entropy of integer order alpha, Eq. (sre):
+ *     M_alpha = 1/(1 - alpha) * log2( (1/d) sum_P |<psi|P|psi>|^{2 alpha} )
+ * for the normalised state, i.e. log2(S_alpha / (d n2^{2 alpha})) / (1 - alpha)
+ * with S_alpha = sum_{x,z} |A_x(z)|^{2 alpha} of the stored state.  The same
+ * XOR-FWHT pass as M2 (Algorithm 1) with the exponent 2 alpha in place of 4;
+ * for x >= 4096 the conjugate symmetry gives sum_z |A_x(z)|^{2 alpha} =
+ * 2^{2 alpha} sum_{z'} [(Re W)^{2 alpha} + (Im W)^{2 alpha}].  alpha = 2 is M2
+ * (bitwise the same as sre_m2).  2 <= alpha <= SRE_MAX_ORDER, else
+ * SRE_EINVAL.  SYNCHRONOUS; result in *m_host; other arguments and errors as
+ * sre_m2.  FP32 modes: terms below the FP32 range (|A|^{2 alpha} < ~1e-45)
+ * count as zero; for a normalised state they are far below the result's
+ * rounding.
+ */
+SRE_API sre_status_t sre_m_alpha(sre_plan_t plan, const void *d_state, int N, int alpha,
+                                 sre_stream_t stream, double *m_host);
+
+/*
+ * sre_sum4_range at Renyi order alpha: d_out[0] = sum over shifts
+ * [x_begin, x_end) of sum_z |A_x(z)|^{2 alpha}, d_out[1] = n2; d_per_x as
+ * there.  Asynchronous; shards add up to S_alpha.  SRE_EINVAL for alpha
+ * outside [2, SRE_MAX_ORDER] or a bad range.
+ */
+SRE_API sre_status_t sre_sum_pow_range(sre_plan_t plan, const void *d_state, int N, int alpha,
+                                       uint64_t x_begin, uint64_t x_end, sre_stream_t stream,
+                                       double *d_out, double *d_per_x);
 
 /*
  * M2 of `count` states of uneven size in one submission (states may have

@@ -102,6 +102,8 @@ def _declare(lib):
         "sre_m2_async": (S, [_vp, _vp, _i, _vp, _vp]),
         "sre_m2_host": (S, [_vp, _vp, _i, _vp, _dp]),
         "sre_sum4_range": (S, [_vp, _vp, _i, _u64, _u64, _vp, _vp, _vp]),
+        "sre_m_alpha": (S, [_vp, _vp, _i, _i, _vp, _dp]),
+        "sre_sum_pow_range": (S, [_vp, _vp, _i, _i, _u64, _u64, _vp, _vp, _vp]),
         "sre_m2_batched": (S, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), _i, _vp, _vp]),
         "sre_selftest_wait_timeout": (S, [_u64, _vp]),
         "sre_server_cfg_default": (None, [ctypes.POINTER(ServerCfg)]),
@@ -313,6 +315,28 @@ class Plan:
             self._h, ctypes.c_void_p(t.data_ptr()), N, int(x_begin), int(x_end), _stream_handle(stream),
             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(px.data_ptr()) if per_x else None),
             "sre_sum4_range")
+        return (out, px) if per_x else out
+
+    def m_alpha(self, t, alpha: int, stream=None) -> float:
+        """sre_m_alpha: stabilizer Renyi entropy of integer order alpha
+        (Eq. (sre)) of a device state (synchronous)."""
+        N = self._state(t)
+        out = ctypes.c_double()
+        _check(load_library().sre_m_alpha(self._h, ctypes.c_void_p(t.data_ptr()), N, int(alpha),
+                                          _stream_handle(stream), ctypes.byref(out)), "sre_m_alpha")
+        return out.value
+
+    def sum_pow_range(self, t, alpha: int, x_begin: int, x_end: int, per_x: bool = False, stream=None):
+        """sre_sum_pow_range: (S_alpha over shifts [x_begin, x_end), n2[,
+        per-shift sums]) as CUDA float64 tensors (asynchronous on `stream`)."""
+        torch = _torch()
+        N = self._state(t)
+        out = torch.empty(2, dtype=torch.float64, device=t.device)
+        px = torch.empty(int(x_end) - int(x_begin), dtype=torch.float64, device=t.device) if per_x else None
+        _check(load_library().sre_sum_pow_range(
+            self._h, ctypes.c_void_p(t.data_ptr()), N, int(alpha), int(x_begin), int(x_end),
+            _stream_handle(stream), ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(px.data_ptr()) if per_x else None), "sre_sum_pow_range")
         return (out, px) if per_x else out
 
     def m2_batched(self, states, out=None, stream=None):

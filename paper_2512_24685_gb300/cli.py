@@ -51,6 +51,7 @@ def main(argv=None):
         p.add_argument("--repeat", type=int, default=1)
         p.add_argument("--tuning", default=None, help="C_LOG,R,D,G2,B1[,S1,S2] of the halved-shift launch")
         p.add_argument("--autotune", action="store_true")
+        p.add_argument("--alpha", type=int, default=2, help="Renyi order (integer >= 2)")
         if name == "range":
             p.add_argument("--x-begin", type=int, required=True)
             p.add_argument("--count", type=int, required=True)
@@ -72,10 +73,18 @@ def main(argv=None):
         t0 = time.perf_counter()
         for _ in range(args.repeat):
             if args.cmd == "m2":
-                out["m2"] = plan.m2(psi)
+                if args.alpha == 2:
+                    out["m2"] = plan.m2(psi)
+                else:
+                    out["alpha"] = args.alpha
+                    out["m_alpha"] = plan.m_alpha(psi, args.alpha)
             else:
                 xe = args.x_begin + args.count
-                res = plan.sum4_range(psi, args.x_begin, xe, per_x=args.per_x)
+                if args.alpha == 2:
+                    res = plan.sum4_range(psi, args.x_begin, xe, per_x=args.per_x)
+                else:
+                    out["alpha"] = args.alpha
+                    res = plan.sum_pow_range(psi, args.alpha, args.x_begin, xe, per_x=args.per_x)
                 sums = res[0] if args.per_x else res
                 torch.cuda.synchronize()
                 out["x_range"] = [args.x_begin, xe]

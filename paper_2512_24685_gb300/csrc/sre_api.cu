@@ -227,10 +227,10 @@ static sre::LargeCfg plan_cfg(sre_plan_t p, int N) {
 
 static sre_status_t enqueue_plan_cfg(sre_plan_t p, const void *d_state, int N, uint64_t xb,
                                      uint64_t xe, cudaStream_t st, double *d_m2, double *d_per_x,
-                                     sre::LargeCfg *cfg);
+                                     sre::LargeCfg *cfg, int alpha = 2);
 
 static sre_status_t enqueue_plan(sre_plan_t p, const void *d_state, int N, uint64_t xb, uint64_t xe,
-                                 cudaStream_t st, double *d_m2, double *d_per_x) {
+                                 cudaStream_t st, double *d_m2, double *d_per_x, int alpha = 2) {
     sre::LargeCfg c;
     sre::LargeCfg *cp = nullptr;
     if (N > sre::kTileBits) {
@@ -238,19 +238,19 @@ static sre_status_t enqueue_plan(sre_plan_t p, const void *d_state, int N, uint6
         if (!sre::large_cfg_fits(p->ws, c, N, 1)) return SRE_EINVAL;
         cp = &c;
     }
-    return enqueue_plan_cfg(p, d_state, N, xb, xe, st, d_m2, d_per_x, cp);
+    return enqueue_plan_cfg(p, d_state, N, xb, xe, st, d_m2, d_per_x, cp, alpha);
 }
 
 static sre_status_t enqueue_plan_cfg(sre_plan_t p, const void *d_state, int N, uint64_t xb,
                                      uint64_t xe, cudaStream_t st, double *d_m2, double *d_per_x,
-                                     sre::LargeCfg *cfg) {
+                                     sre::LargeCfg *cfg, int alpha) {
     cudaError_t e;
     if (sre::tc_mode_available(p->mode))
         e = sre::tc_enqueue_m2(p->ws, p->dev, d_state, p->dtype, N, xb, xe, p->mode, st, d_m2,
-                               d_per_x, p->wait_ns, cfg);
+                               d_per_x, p->wait_ns, cfg, alpha);
     else
         e = sre::enqueue_m2(p->ws, p->dev, d_state, p->dtype, N, xb, xe, p->mode, st, d_m2,
-                            d_per_x, p->wait_ns, cfg);
+                            d_per_x, p->wait_ns, cfg, alpha);
     return e == cudaSuccess ? SRE_OK : cuda_fail(e);
 }
 
@@ -468,6 +468,31 @@ sre_status_t sre_sum4_range(sre_plan_t p, const void *d_state, int N, uint64_t x
     if (d_per_x && N <= sre::kTileBits) return SRE_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     s = enqueue_plan(p, d_state, N, x_begin, x_end, st, nullptr, d_per_x);
+    if (s != SRE_OK) return s;
+    cudaError_t e = sre::enqueue_copy_sums(p->ws, d_out, st);
+    return e == cudaSuccess ? SRE_OK : cuda_fail(e);
+}
+
+sre_status_t sre_m_alpha(sre_plan_t p, const void *d_state, int N, int alpha, sre_stream_t stream,
+                         double *m_host) {
+    sre_status_t s = check_state(p, d_state, N);
+    if (s != SRE_OK) return s;
+    if (!m_host || alpha < 2 || alpha > SRE_MAX_ORDER) return SRE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    s = enqueue_plan(p, d_state, N, 0, 1ull << N, st, nullptr, nullptr, alpha);
+    if (s != SRE_OK) return s;
+    return read_result(p, st, m_host);
+}
+
+sre_status_t sre_sum_pow_range(sre_plan_t p, const void *d_state, int N, int alpha, uint64_t x_begin,
+                               uint64_t x_end, sre_stream_t stream, double *d_out, double *d_per_x) {
+    sre_status_t s = check_state(p, d_state, N);
+    if (s != SRE_OK) return s;
+    if (!d_out || alpha < 2 || alpha > SRE_MAX_ORDER || x_begin >= x_end || x_end > (1ull << N))
+        return SRE_EINVAL;
+    if (d_per_x && N <= sre::kTileBits) return SRE_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    s = enqueue_plan(p, d_state, N, x_begin, x_end, st, nullptr, d_per_x, alpha);
     if (s != SRE_OK) return s;
     cudaError_t e = sre::enqueue_copy_sums(p->ws, d_out, st);
     return e == cudaSuccess ? SRE_OK : cuda_fail(e);

@@ -25,6 +25,6 @@ bool tc_mode_available(sre_mode_t mode);
 cudaError_t tc_enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d_state,
                           sre_dtype_t dtype, int N, uint64_t x_begin, uint64_t x_end,
                           sre_mode_t mode, cudaStream_t stream, double *d_m2, double *d_per_x,
-                          long long wait_ns, LargeCfg *cfg_half);
+                          long long wait_ns, LargeCfg *cfg_half, int alpha = 2);
 
 }  // namespace sre

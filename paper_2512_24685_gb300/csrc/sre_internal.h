@@ -105,10 +105,11 @@ void workspace_free(Workspace *ws);
 // The result block (m2, S, n2, status) lands in ws->result; if d_m2 is not
 // null M2 is also written there; if d_per_x is not null and N > 12 each
 // shift's sum is written there.  mode: SRE_MODE_FP32 or SRE_MODE_FP64.
+// alpha: Renyi order (2: M2; larger integers: M_alpha, S the order-alpha sum).
 cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d_state,
                        sre_dtype_t dtype, int N, uint64_t x_begin, uint64_t x_end,
                        sre_mode_t mode, cudaStream_t stream, double *d_m2, double *d_per_x,
-                       long long wait_ns, LargeCfg *cfg_override);
+                       long long wait_ns, LargeCfg *cfg_override, int alpha = 2);
 
 // ---- batched evaluation: states grouped in classes of equal N.
 struct BatchClass {

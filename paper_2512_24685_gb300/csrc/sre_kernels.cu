@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
                                                     long long tiles_per_state,
                                                     uint64_t x_begin, uint64_t x_end,
                                                     long long ntiles,
-                                                    double *__restrict__ part) {
+                                                    double *__restrict__ part, int alpha) {
     // Single state: psis == nullptr.  Several states of the same N: psis[s] is
     // state s and tiles are numbered state-major.  Tile g's sum goes to
     // part[g] (fixed-order tree inside the tile), so a state's partials do not
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_small(const v2_t<R> *__restrict__ 
         }
         tile_fwht<NB, R>(v, bufA, bufB, tid);
         // block_sum's barriers also protect bufB before the next tile
-        const double s = block_sum((double)sum_abs4<R>(v), red);
+        const double s = block_sum((double)sum_order<R, false>(v, alpha), red);
         if (tid == 0) part[g] = s;
     }
 }
@@ -151,18 +151,27 @@ __device__ __forceinline__ double m2_from(double S, double n2, int N, bool bad) 
                : -(log2(S) - (double)N - 4.0 * log2(n2));
 }
 
+// Eq. (sre) at integer order alpha: M_alpha = log2(S / (d n2^(2 alpha))) /
+// (1 - alpha); order 2 is m2_from.
+__device__ __forceinline__ double malpha_from(double S, double n2, int N, int alpha, bool bad) {
+    if (alpha == 2) return m2_from(S, n2, N, bad);
+    return bad ? __longlong_as_double(0x7ff8000000000000ll)
+               : (log2(S) - (double)N - 2.0 * alpha * log2(n2)) / (1.0 - alpha);
+}
+
 // One warp: S from the partial segments [o1, o1+n1) and [o2, o2+n2), n2 from
 // the norm partials, M2 and the status.
 __global__ void k_finalize(const double *__restrict__ parts, long long o1, long long n1, long long o2,
                            long long n2c, const double *__restrict__ npart, int nn, int N,
-                           const int *flags, const int *status, Result *res, double *d_m2) {
+                           const int *flags, const int *status, Result *res, double *d_m2,
+                           int alpha) {
     const double S = warp_sum_segments(parts, o1, n1, o2, n2c);
     const double n2 = warp_sum_segments(npart, 0, nn, 0, 0);
     if (threadIdx.x == 0) {
         int st = *status;
         if (st == 0 && (*flags & kFlagNonFinite)) st = SRE_ENONFINITE;
         if (st == 0 && !(n2 > 0.0)) st = SRE_EZERO;
-        const double m2 = m2_from(S, n2, N, st != 0);
+        const double m2 = malpha_from(S, n2, N, alpha, st != 0);
         res->m2 = m2;
         res->S = S;
         res->n2 = n2;
@@ -339,7 +348,7 @@ template <typename R, int NB>
 static cudaError_t launch_small_nb(const void *psi, const void *const *psis, int nstates,
                                    uint64_t x_begin, uint64_t x_end, double *part, int part_cap,
                                    const DeviceInfo &dev, cudaStream_t st, int *nparts,
-                                   int forced_grid = 0) {
+                                   int forced_grid = 0, int alpha = 2) {
     const size_t smem = tile_smem_bytes(sizeof(v2_t<R>));
     auto kern = k_small<R, NB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -353,7 +362,7 @@ static cudaError_t launch_small_nb(const void *psi, const void *const *psis, int
                                      : (int)std::min<long long>(ntiles, (long long)dev.sms * occ);
     if (grid < 1) return cudaErrorInvalidValue;
     kern<<<grid, kThreads, smem, st>>>(reinterpret_cast<const v2_t<R> *>(psi), psis, tps, x_begin,
-                                       x_end, ntiles, part);
+                                       x_end, ntiles, part, alpha);
     *nparts = (int)ntiles;
     return cudaGetLastError();
 }
@@ -362,10 +371,10 @@ template <typename R>
 static cudaError_t launch_small(int N, const void *psi, const void *const *psis, int nstates,
                                 uint64_t xb, uint64_t xe, double *part, int part_cap,
                                 const DeviceInfo &dev, cudaStream_t st, int *nparts,
-                                int forced_grid = 0) {
+                                int forced_grid = 0, int alpha = 2) {
     switch (N) {
 #define SRE_CASE(n) \
-    case n: return launch_small_nb<R, n>(psi, psis, nstates, xb, xe, part, part_cap, dev, st, nparts, forced_grid);
+    case n: return launch_small_nb<R, n>(psi, psis, nstates, xb, xe, part, part_cap, dev, st, nparts, forced_grid, alpha);
         SRE_CASE(1) SRE_CASE(2) SRE_CASE(3) SRE_CASE(4) SRE_CASE(5) SRE_CASE(6)
         SRE_CASE(7) SRE_CASE(8) SRE_CASE(9) SRE_CASE(10) SRE_CASE(11) SRE_CASE(12)
 #undef SRE_CASE
@@ -462,6 +471,7 @@ static cudaError_t make_large_args(LargeArgs *a, const Workspace &ws, const Devi
     A.B1_log = std::max(0, std::min(c.B1_log, A.h2));
     A.stage1 = c.stage1;
     A.stage2 = c.stage2;
+    A.alpha = 2;
     A.P1 = 1 << (A.h2 - A.B1_log);
     A.P2 = (1 << c.C_log) << (A.h2 - A.G2_log);
     A.n_items = A.n_chunks * (long long)(A.P1 + A.P2);
@@ -492,7 +502,7 @@ template <typename R>
 static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, const void *psi, int N,
                                 uint64_t x_begin, uint64_t x_end, cudaStream_t st, double *d_m2,
                                 double *d_per_x, long long wait_ns, LargeCfg *cfg_override,
-                                int tc_kind) {
+                                int tc_kind, int alpha) {
     cudaError_t e;
     const uint64_t d = 1ull << N;
     if ((e = cudaMemsetAsync(ws.flags, 0, sizeof(int), st)) != cudaSuccess) return e;
@@ -507,7 +517,7 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
         int np = 0;
         if (ws.ev_begin && (e = cudaEventRecord(ws.ev_begin, st)) != cudaSuccess) return e;
         if ((e = launch_small<R>(N, psi, nullptr, 1, x_begin, x_end, ws.part, ws.part_cap, dev, st,
-                                 &np)) != cudaSuccess)
+                                 &np, 0, alpha)) != cudaSuccess)
             return e;
         if (ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
         ws.main_kernel = "k_small";
@@ -535,6 +545,7 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
                                      d_per_x ? d_per_x + (xb - x_begin) : nullptr, wait_ns,
                                      cfg_override && half ? cfg_override : nullptr, &grid)) != cudaSuccess)
                 return e;
+            a.alpha = alpha;
             if (half && tc_kind)
                 e = launch_large_tc(a, grid, st, tc_kind);
             else if (half)
@@ -552,7 +563,7 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
         nparts = (long long)chunks;
     }
     k_finalize<<<1, 32, 0, st>>>(parts, 0, seg1, seg1, nparts - seg1, ws.npart, kNormBlocks, N,
-                                 ws.flags, ws.status, ws.result, d_m2);
+                                 ws.flags, ws.status, ws.result, d_m2, alpha);
     return cudaGetLastError();
 }
 
@@ -599,14 +610,14 @@ cudaError_t enqueue_m2_fixed(const Workspace &ws, const DeviceInfo &dev, const v
         nparts = (long long)chunks;
     }
     k_finalize<<<1, 32, 0, st>>>(parts, 0, seg1, seg1, nparts - seg1, ws.npart, kNormBlocks, N, ws.flags,
-                                 ws.status, ws.result, d_m2);
+                                 ws.status, ws.result, d_m2, 2);
     return cudaGetLastError();
 }
 
 cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d_state,
                        sre_dtype_t dtype, int N, uint64_t x_begin, uint64_t x_end,
                        sre_mode_t mode, cudaStream_t stream, double *d_m2, double *d_per_x,
-                       long long wait_ns, LargeCfg *cfg_override) {
+                       long long wait_ns, LargeCfg *cfg_override, int alpha) {
     const bool fp64 = (mode == SRE_MODE_FP64);
     const int want = fp64 ? SRE_C128 : SRE_C64;
     const void *psi = d_state;
@@ -629,9 +640,9 @@ cudaError_t enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d
     const int tc_kind = mode == SRE_MODE_BF16_SPLIT ? 1 : mode == SRE_MODE_FP16_SPLIT ? 2 : 0;
     if (fp64)
         return enqueue_m2_t<double>(ws, dev, psi, N, x_begin, x_end, stream, d_m2, d_per_x, wait_ns,
-                                    cfg_override, 0);
+                                    cfg_override, 0, alpha);
     return enqueue_m2_t<float>(ws, dev, psi, N, x_begin, x_end, stream, d_m2, d_per_x, wait_ns,
-                               cfg_override, tc_kind);
+                               cfg_override, tc_kind, alpha);
 }
 
 // --------------------------------------------------------- wait self test
@@ -774,6 +785,7 @@ static cudaError_t enqueue_batch_class_t(const Workspace &ws, const DeviceInfo &
         A.B1_log = std::max(0, std::min(c.B1_log, A.h2));
         A.stage1 = c.stage1;
         A.stage2 = c.stage2;
+        A.alpha = 2;
         A.n_chunks = cps * L.S;
         A.D = (int)std::max<long long>(1, std::min<long long>(std::min(c.D, c.R - 1), A.n_chunks));
         A.P1 = 1 << (A.h2 - A.B1_log);

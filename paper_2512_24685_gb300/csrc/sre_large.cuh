@@ -41,7 +41,9 @@ using namespace dev;
 // Halving (half = 1, shifts x >= 4096).  With pivot j = the highest set bit
 // of x, g_x(t ^ x) = conj(g_x(t)) pairs every t with t_j = 1 to one with
 // t_j = 0, and sum_z |A_x(z)|^4 = 16 sum_{z'} [(Re W(z'))^4 + (Im W(z'))^4]
-// where W is the (N-1)-bit transform of g_x restricted to t_j = 0.  Since
+// where W is the (N-1)-bit transform of g_x restricted to t_j = 0 (A is
+// 2 Re W or 2i Im W, so at Renyi order alpha the exponents are 2 alpha and
+// the factor 2^(2 alpha)).  Since
 // j >= 12, the restriction removes one high bit: block t'_h maps to
 // t_h = t'_h with a zero inserted at bit j - 12, and h2 = N - 13.
 //
@@ -59,6 +61,7 @@ struct LargeArgs {
     uint64_t x0;               // x_begin rounded down to a chunk boundary
     int C_log, R, D, G2_log, B1_log;
     int stage1, stage2;        // staged copy paths enabled (LargeCfg)
+    int alpha;                 // Renyi order (2: M2)
     long long n_chunks;
     int P1, P2;                // items per chunk in pass 1 / pass 2
     long long n_items;
@@ -191,6 +194,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
     V *scratch = reinterpret_cast<V *>(a.scratch);
     constexpr int zsub_bits = kTileBits - H2;     // z entries per block in pass 2
     const int ipx_log = H2 - a.G2_log;            // pass-2 items per shift (log2)
+    // halved shifts: sum_z |A|^(2 alpha) = 2^(2 alpha) sum_z' [(Re W)^(2 alpha) +
+    // (Im W)^(2 alpha)] (16 at alpha = 2)
+    const double hfac = (double)(1ull << (2 * a.alpha));
 
     const int warp = tid >> 5, lane = tid & 31;
     constexpr int kWarps = kThreads / 32;
@@ -405,8 +411,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
                         }
                         sphase ^= 1u << st;
                         const unsigned char *stage = reinterpret_cast<const unsigned char *>(st ? bufC : bufB);
-                        const float s = p2_tile<H2, HALF>(stage, reinterpret_cast<float2 *>(bufA), pl);
-                        acc += (HALF ? 16.0 : 1.0) * (double)s;
+                        const float s = p2_tile<H2, HALF>(stage, reinterpret_cast<float2 *>(bufA), pl, a.alpha);
+                        acc += (HALF ? hfac : 1.0) * (double)s;
                         if (gb + 2 < ntiles) {
                             __syncthreads();  // every thread has read stage st
                             if (tid == 0) {
@@ -437,10 +443,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
                     V *bB = (tcount & 1) ? bufC : bufB;
                     if (H2 > 8) ++tcount;
                     tile_fwht<H2, R>(v, bufA, bB, tid);
-                    if (HALF)
-                        acc += 16.0 * (double)sum_re4_im4<R>(v);
-                    else
-                        acc += (double)sum_abs4<R>(v);
+                    acc += (HALF ? hfac : 1.0) * (double)sum_order<R, HALF>(v, a.alpha);
                 }
             }
             }

@@ -168,10 +168,12 @@ __device__ __forceinline__ P2Lane p2_lane(int lane, int warp) {
 }
 
 // Transform one staged tile and return this thread's share of the quartic
-// sum: sum (Re W)^4 + (Im W)^4 (HALF) or sum |W|^4.  xbuf is the warp-local
+// sum: sum (Re W)^4 + (Im W)^4 (HALF) or sum |W|^4 (exponents 2 alpha in place
+// of 4 at Renyi order alpha).  xbuf is the warp-local
 // exchange buffer (kTileSlots entries, warp w uses [544 w, 544 w + 544)).
 template <int H2, bool HALF>
-__device__ __forceinline__ float p2_tile(const unsigned char *stage, float2 *xbuf, const P2Lane &p) {
+__device__ __forceinline__ float p2_tile(const unsigned char *stage, float2 *xbuf, const P2Lane &p,
+                                         int alpha) {
     using L = P2Stage<H2>;
     using T = cx_t<float>;
     T v[16];
@@ -187,7 +189,7 @@ __device__ __forceinline__ float p2_tile(const unsigned char *stage, float2 *xbu
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = xb[p.xb + pad(L::q_of(L::e9_regB(i)))];
     reg_stages_mask<L::maskB(), float>(v);
-    return HALF ? sum_re4_im4<float>(v) : sum_abs4<float>(v);
+    return sum_order<float, HALF>(v, alpha);
 }
 
 // ------------------------------------------------- TMA / mbarrier helpers

@@ -53,10 +53,10 @@ bool tc_mode_available(sre_mode_t mode) {
 cudaError_t tc_enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d_state,
                           sre_dtype_t dtype, int N, uint64_t x_begin, uint64_t x_end,
                           sre_mode_t mode, cudaStream_t stream, double *d_m2, double *d_per_x,
-                          long long wait_ns, LargeCfg *cfg_half) {
+                          long long wait_ns, LargeCfg *cfg_half, int alpha) {
     if (N > kTileBits + 9) return cudaErrorNotSupported;
     return enqueue_m2(ws, dev, d_state, dtype, N, x_begin, x_end, mode, stream, d_m2, d_per_x, wait_ns,
-                      cfg_half);
+                      cfg_half, alpha);
 }
 
 }  // namespace sre

@@ -214,6 +214,47 @@ __device__ __forceinline__ R sum_re4_im4(const cx_t<R> (&v)[16]) {
     return a + b;
 }
 
+// Order alpha of Eq. (sre): sum_i (|F_i|^2)^alpha over the thread's 16
+// entries (integer alpha >= 2, a product of alpha factors), in R.
+template <typename R>
+__device__ __forceinline__ R sum_abs_pow(const cx_t<R> (&v)[16], int alpha) {
+    R s = R(0);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        R re, im;
+        Cx<R>::unpack(Cx<R>::mul(v[i], v[i]), re, im);
+        const R m = re + im;
+        R p = m;
+        for (int k = 1; k < alpha; ++k) p *= m;
+        s += p;
+    }
+    return s;
+}
+
+// Order alpha, halved shifts: sum_i (Re F_i)^(2 alpha) + (Im F_i)^(2 alpha).
+template <typename R>
+__device__ __forceinline__ R sum_re_im_pow(const cx_t<R> (&v)[16], int alpha) {
+    cx_t<R> acc = Cx<R>::zero();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const cx_t<R> sq = Cx<R>::mul(v[i], v[i]);
+        cx_t<R> p = sq;
+        for (int k = 1; k < alpha; ++k) p = Cx<R>::mul(p, sq);
+        acc = Cx<R>::add(acc, p);
+    }
+    R a, b;
+    Cx<R>::unpack(acc, a, b);
+    return a + b;
+}
+
+// The thread's share of the order-alpha sum (HALF: the halved-shift form);
+// order 2 takes the M2 reductions above unchanged.
+template <typename R, bool HALF>
+__device__ __forceinline__ R sum_order(const cx_t<R> (&v)[16], int alpha) {
+    if (alpha == 2) return HALF ? sum_re4_im4<R>(v) : sum_abs4<R>(v);
+    return HALF ? sum_re_im_pow<R>(v, alpha) : sum_abs_pow<R>(v, alpha);
+}
+
 // Deterministic block-wide FP64 sum (fixed tree); result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double *red /* kThreads/32 */) {
 #pragma unroll

@@ -385,6 +385,25 @@ def run_fp64_check(binding, torch, W, N=16):
     return res
 
 
+def run_orders(binding, torch, W, N, fp32_ms, m2_val, orders=(3, 4)):
+    """Higher Renyi orders (Eq. (sre)) on the benchmark's N = 20 state: one
+    timed sre_m_alpha per order (after a warm-up), beside the M2 time, with
+    the tuning the autotuner picked for M2."""
+    import numpy as np
+    psi = torch.from_numpy(W.haar_state(N, W.config_seed(CONFIG_INDEX, 0), np.complex64)).cuda()
+    out = {"N": N, "m2_kernel_ms": fp32_ms, "m2": m2_val}
+    with binding.Plan(N, "c64") as p:
+        p.autotune(N)
+        for a in orders:
+            p.m_alpha(psi, a)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m = p.m_alpha(psi, a)
+            ms = (time.perf_counter() - t0) * 1e3
+            out[f"alpha{a}"] = {"ms": ms, "m_alpha": m, "pauli_terms_per_s": 4.0 ** N / (ms / 1e3)}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args):
@@ -544,6 +563,10 @@ def run_gpu(args):
                                                       m2_val, peaks)
         except Exception as exc:
             extras["tensor_modes"] = {"error": repr(exc)}
+        try:
+            extras["orders"] = run_orders(binding, torch, W, N, statistics.mean(kern_ms), m2_val)
+        except Exception as exc:
+            extras["orders"] = {"error": repr(exc)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -247,12 +247,50 @@ __device__ __forceinline__ R sum_re_im_pow(const cx_t<R> (&v)[16], int alpha) {
     return a + b;
 }
 
+// Orders 3 and 4 with the power unrolled at compile time (same products in
+// the same order as the loops above).
+template <typename R, int A>
+__device__ __forceinline__ R sum_abs_pow_c(const cx_t<R> (&v)[16]) {
+    R s = R(0);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        R re, im;
+        Cx<R>::unpack(Cx<R>::mul(v[i], v[i]), re, im);
+        const R m = re + im;
+        R p = m;
+#pragma unroll
+        for (int k = 1; k < A; ++k) p *= m;
+        s += p;
+    }
+    return s;
+}
+
+template <typename R, int A>
+__device__ __forceinline__ R sum_re_im_pow_c(const cx_t<R> (&v)[16]) {
+    cx_t<R> acc = Cx<R>::zero();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const cx_t<R> sq = Cx<R>::mul(v[i], v[i]);
+        cx_t<R> p = sq;
+#pragma unroll
+        for (int k = 1; k < A; ++k) p = Cx<R>::mul(p, sq);
+        acc = Cx<R>::add(acc, p);
+    }
+    R a, b;
+    Cx<R>::unpack(acc, a, b);
+    return a + b;
+}
+
 // The thread's share of the order-alpha sum (HALF: the halved-shift form);
 // order 2 takes the M2 reductions above unchanged.
 template <typename R, bool HALF>
 __device__ __forceinline__ R sum_order(const cx_t<R> (&v)[16], int alpha) {
-    if (alpha == 2) return HALF ? sum_re4_im4<R>(v) : sum_abs4<R>(v);
-    return HALF ? sum_re_im_pow<R>(v, alpha) : sum_abs_pow<R>(v, alpha);
+    switch (alpha) {
+        case 2: return HALF ? sum_re4_im4<R>(v) : sum_abs4<R>(v);
+        case 3: return HALF ? sum_re_im_pow_c<R, 3>(v) : sum_abs_pow_c<R, 3>(v);
+        case 4: return HALF ? sum_re_im_pow_c<R, 4>(v) : sum_abs_pow_c<R, 4>(v);
+        default: return HALF ? sum_re_im_pow<R>(v, alpha) : sum_abs_pow<R>(v, alpha);
+    }
 }
 
 // Deterministic block-wide FP64 sum (fixed tree); result valid in thread 0.

@@ -227,6 +227,28 @@ SRE_API sre_status_t sre_m_alpha(sre_plan_t plan, const void *d_state, int N, in
                                  sre_stream_t stream, double *m_host);
 
 /*
+ * Random-circuit quench dynamics (the paper's Example 2), evolved on the
+ * device: S independent realizations of an N-qubit open chain start in
+ * |0...0>; step t applies a two-qubit gate to every even bond (0,1), (2,3),
+ * ... and then to every odd bond (1,2), (3,4), ...; after every step M2 of
+ * every realization is evaluated (the batched path, in the plan's mode).
+ *   d_gates  device, T * S * (N - 1) gates of 16 complex128 (re, im) each:
+ *            gate (t, s, b) at offset ((t S + s)(N - 1) + b) * 16, row-major,
+ *            acting on the index 2 b_{q+1} + b_q of bond (q, q+1); b < N/2 is
+ *            the even bond q = 2b, larger b the odd bond q = 2(b - N/2) + 1.
+ *            For Example 2 every gate is Haar-random on U(4).
+ *   d_states device, S * 2^N complex128, caller-owned scratch; holds the
+ *            final states on return.
+ *   d_m2_out device, T * S doubles: M2 of realization s after step t at
+ *            t * S + s.
+ * The plan's dtype must be SRE_C128 and 2 <= N <= its N, 1 <= S <= 65535,
+ * T >= 1 (SRE_EINVAL otherwise; SRE_EALIGN for pointers not 16-byte aligned,
+ * d_m2_out 8-byte).  Gates are applied in FP64.  Asynchronous on `stream`.
+ */
+SRE_API sre_status_t sre_brickwork_m2_series(sre_plan_t plan, int N, int S, int T, const void *d_gates,
+                                             void *d_states, sre_stream_t stream, double *d_m2_out);
+
+/*
  * sre_sum4_range at Renyi order alpha: d_out[0] = sum over shifts
  * [x_begin, x_end) of sum_z |A_x(z)|^{2 alpha}, d_out[1] = n2; d_per_x as
  * there.  Asynchronous; shards add up to S_alpha.  SRE_EINVAL for alpha

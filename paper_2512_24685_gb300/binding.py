@@ -103,6 +103,7 @@ def _declare(lib):
         "sre_m2_host": (S, [_vp, _vp, _i, _vp, _dp]),
         "sre_sum4_range": (S, [_vp, _vp, _i, _u64, _u64, _vp, _vp, _vp]),
         "sre_m_alpha": (S, [_vp, _vp, _i, _i, _vp, _dp]),
+        "sre_brickwork_m2_series": (S, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
         "sre_sum_pow_range": (S, [_vp, _vp, _i, _i, _u64, _u64, _vp, _vp, _vp]),
         "sre_m2_batched": (S, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), _i, _vp, _vp]),
         "sre_selftest_wait_timeout": (S, [_u64, _vp]),
@@ -338,6 +339,25 @@ class Plan:
             _stream_handle(stream), ctypes.c_void_p(out.data_ptr()),
             ctypes.c_void_p(px.data_ptr()) if per_x else None), "sre_sum_pow_range")
         return (out, px) if per_x else out
+
+    def brickwork_m2_series(self, gates, states=None, stream=None):
+        """sre_brickwork_m2_series: M2 after every step of brickwork circuit
+        dynamics evolved on the device.  gates: complex128 CUDA tensor of
+        shape (T, S, N - 1, 4, 4) (even bonds then odd bonds per step);
+        states: optional complex128 CUDA tensor (S, 2^N) that receives the
+        final states.  Returns (M2 as a (T, S) float64 CUDA tensor, states)."""
+        torch = _torch()
+        T, S, nb = int(gates.shape[0]), int(gates.shape[1]), int(gates.shape[2])
+        N = nb + 1
+        if gates.dtype != torch.complex128 or tuple(gates.shape[3:]) != (4, 4) or not gates.is_contiguous():
+            raise ValueError("gates must be a contiguous complex128 tensor of shape (T, S, N-1, 4, 4)")
+        if states is None:
+            states = torch.empty((S, 1 << N), dtype=torch.complex128, device=gates.device)
+        out = torch.empty((T, S), dtype=torch.float64, device=gates.device)
+        _check(load_library().sre_brickwork_m2_series(
+            self._h, N, S, T, ctypes.c_void_p(gates.data_ptr()), ctypes.c_void_p(states.data_ptr()),
+            _stream_handle(stream), ctypes.c_void_p(out.data_ptr())), "sre_brickwork_m2_series")
+        return out, states
 
     def m2_batched(self, states, out=None, stream=None):
         """sre_m2_batched: M2 of many device states of uneven N (float64 CUDA tensor)."""

@@ -50,6 +50,8 @@ struct sre_plan_s {
     bool has_tuned[SRE_MAX_QUBITS + 1] = {};
     void *tune_state = nullptr;                     // synthetic state for autotuning
     sre::LargeCfg batch_cfg[SRE_MAX_QUBITS + 1];    // configurations handed to batches
+    double *d_series = nullptr;                     // one step's M2 values (brickwork series)
+    int d_series_cap = 0;
 };
 
 namespace {
@@ -204,6 +206,7 @@ sre_status_t sre_plan_destroy(sre_plan_t p) {
     cudaFreeHost(p->h_result);
     cudaFree(p->d_stage);
     cudaFree(p->tune_state);
+    cudaFree(p->d_series);
     delete p;
     return SRE_OK;
 }
@@ -496,6 +499,41 @@ sre_status_t sre_sum_pow_range(sre_plan_t p, const void *d_state, int N, int alp
     if (s != SRE_OK) return s;
     cudaError_t e = sre::enqueue_copy_sums(p->ws, d_out, st);
     return e == cudaSuccess ? SRE_OK : cuda_fail(e);
+}
+
+sre_status_t sre_brickwork_m2_series(sre_plan_t p, int N, int S, int T, const void *d_gates,
+                                     void *d_states, sre_stream_t stream, double *d_m2_out) {
+    if (!p || !d_gates || !d_states || !d_m2_out) return SRE_EINVAL;
+    if (p->dtype != SRE_C128 || N < 2 || N > p->N || S < 1 || S > 65535 || T < 1) return SRE_EINVAL;
+    if (((uintptr_t)d_gates) % 16 || ((uintptr_t)d_states) % 16 || ((uintptr_t)d_m2_out) % 8)
+        return SRE_EALIGN;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (p->d_series_cap < S) {
+        cudaFree(p->d_series);
+        p->d_series = nullptr;
+        p->d_series_cap = 0;
+        if ((e = cudaMalloc(&p->d_series, sizeof(double) * (size_t)S)) != cudaSuccess) return cuda_fail(e);
+        p->d_series_cap = S;
+    }
+    std::vector<const void *> ptrs((size_t)S);
+    std::vector<int> Ns((size_t)S, N);
+    for (int s = 0; s < S; ++s) ptrs[s] = (const char *)d_states + ((size_t)s << N) * 16;
+    if ((e = sre::evolve_init(d_states, N, S, p->dev, st)) != cudaSuccess) return cuda_fail(e);
+    p->ws.launches += 1;
+    for (int t = 0; t < T; ++t) {
+        if ((e = sre::evolve_brickwork_step(d_states, N, S, t, d_gates, p->dev, st)) != cudaSuccess)
+            return cuda_fail(e);
+        p->ws.launches += (unsigned long long)(N - 1);
+        // every step's batch has the same states and output, so after the
+        // first step the batched path replays its captured graph
+        sre_status_t s = sre_m2_batched(p, ptrs.data(), Ns.data(), S, stream, p->d_series);
+        if (s != SRE_OK) return s;
+        if ((e = cudaMemcpyAsync(d_m2_out + (size_t)t * S, p->d_series, sizeof(double) * (size_t)S,
+                                 cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    return SRE_OK;
 }
 
 sre_status_t sre_selftest_wait_timeout(uint64_t wait_ns, sre_stream_t stream) {

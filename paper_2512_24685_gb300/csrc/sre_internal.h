@@ -136,6 +136,12 @@ cudaError_t enqueue_batch_finalize(const Workspace &ws, const void *seg, const d
                                    cudaStream_t st);
 cudaError_t enqueue_convert(const void *src, sre_dtype_t from, void *dst, int N, cudaStream_t st);
 
+// Brickwork circuit dynamics (sre_evolve.cu): S complex128 states of N
+// qubits set to |0...0>; one step t of even-bond then odd-bond gates.
+cudaError_t evolve_init(void *d_states, int N, int S, const DeviceInfo &dev, cudaStream_t st);
+cudaError_t evolve_brickwork_step(void *d_states, int N, int S, int t, const void *d_gates,
+                                  const DeviceInfo &dev, cudaStream_t st);
+
 // Bounded-wait self test (see sre_selftest_wait_timeout).
 cudaError_t run_wait_selftest(long long wait_ns, cudaStream_t st, int *status_out);
 

@@ -220,3 +220,17 @@ def uneven_batch_spec(count: int = 512, n_lo: int = 12, n_hi: int = 18,
     Ns = rng.integers(n_lo, n_hi + 1, size=count)
     depths = rng.integers(1, depth_hi + 1, size=count)
     return [(int(n), int(t), config_seed(config_index, i)) for i, (n, t) in enumerate(zip(Ns, depths))]
+
+
+def brickwork_gate_tensor(N: int, S: int, T: int, config_index: int = 4) -> np.ndarray:
+    """Gates of S brickwork realizations over T steps, (T, S, N-1, 4, 4)
+    complex128, in the order applied (per step: even bonds, then odd bonds);
+    realization s draws brickwork_gates(N, T, config_seed(config_index, s)),
+    so the same gates drive brickwork_state."""
+    out = np.empty((T, S, N - 1, 4, 4), dtype=np.complex128)
+    for s in range(S):
+        gates = brickwork_gates(N, T, config_seed(config_index, s))
+        for t in range(T):
+            for b in range(N - 1):
+                out[t, s, b] = gates[t * (N - 1) + b][1]
+    return out

@@ -410,6 +410,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
                             if (lane == 0) atomicCAS(a.status, 0, (int)SRE_ETIMEDOUT);
                         }
                         sphase ^= 1u << st;
+                        {
+                            // the tile is in shared memory: drop its 256 scratch
+                            // lines (2^H2 rows x 2^(8 - H2) lines) from L2 now,
+                            // one per thread, before they can be written back
+                            constexpr int kLpr = 1 << (8 - H2);
+                            const V *xb = slot_base + ((size_t)xl << lgx);
+                            discard_l2_line(xb + ((size_t)(tid / kLpr) << kTileBits) +
+                                            ((zb0 + gb) << zsub_bits) + (tid % kLpr) * 16);
+                        }
                         const unsigned char *stage = reinterpret_cast<const unsigned char *>(st ? bufC : bufB);
                         const float s = p2_tile<H2, HALF>(stage, reinterpret_cast<float2 *>(bufA), pl, a.alpha);
                         acc += (HALF ? hfac : 1.0) * (double)s;
@@ -451,11 +460,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
             // All warps' loads of this item are complete after this barrier:
             // drop the item's scratch lines from L2 without write-back (dead
-            // data; the next chunk in this slot rewrites them).  The drops
-            // precede this item's arrivals, hence the slot's release.
+            // data; the next chunk in this slot rewrites them; the staged path
+            // dropped each tile's lines as it arrived).  The drops precede
+            // this item's arrivals, hence the slot's release.
             __syncthreads();
             constexpr int kLineElems = 128 / (int)sizeof(V);
-            if (((1 << zsub_bits) >= kLineElems) && x >= a.x_begin && x < a.x_end) {
+            if (((1 << zsub_bits) >= kLineElems) && !staged2 && x >= a.x_begin && x < a.x_end) {
                 const V *xb = slot_base + ((size_t)xl << lgx);
                 constexpr int lines_per_row = ((1 << zsub_bits) >= kLineElems) ? (1 << zsub_bits) / kLineElems : 1;
                 constexpr int lines_per_tile = kTile / kLineElems;

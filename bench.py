@@ -404,6 +404,29 @@ def run_orders(binding, torch, W, N, fp32_ms, m2_val, orders=(3, 4)):
     return out
 
 
+def run_brickwork(binding, torch, W, cases=((14, 100, 20), (16, 100, 4))):
+    """Example 2's dynamics on the device: S realizations of N-qubit Haar
+    brickwork circuits from |0...0>, T steps, M2 of every realization after
+    every step (sre_brickwork_m2_series, FP32 M2 of complex128 states)."""
+    import math
+    out = {}
+    for N, S, T in cases:
+        gates = torch.from_numpy(W.brickwork_gate_tensor(N, S, T)).cuda()
+        with binding.Plan(N, "c128") as p:
+            p.brickwork_m2_series(gates[:1])  # warm-up (first-step graph capture)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m2, _ = p.brickwork_m2_series(gates)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+        last = m2[-1].double()
+        out[f"N{N}"] = {"realizations": S, "steps": T, "ms": ms, "ms_per_step": ms / T,
+                        "pauli_terms_per_s": S * T * 4.0 ** N / (ms / 1e3),
+                        "m2_last_step_mean": float(last.mean()), "m2_first_step_mean": float(m2[0].double().mean()),
+                        "haar_value": math.log2(2 ** N + 3) - 2}
+    return out
+
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the halved
 # two-pass launch, from one ncu capture of a 16384-shift slice at N = 20 in
 # the tuning below (3.502 GB read + 28.413 GB written), scaled by shifts to
@@ -587,6 +610,10 @@ def run_gpu(args):
             extras["orders"] = run_orders(binding, torch, W, N, statistics.mean(kern_ms), m2_val)
         except Exception as exc:
             extras["orders"] = {"error": repr(exc)}
+        try:
+            extras["brickwork_dynamics"] = run_brickwork(binding, torch, W)
+        except Exception as exc:
+            extras["brickwork_dynamics"] = {"error": repr(exc)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

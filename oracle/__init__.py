@@ -220,3 +220,33 @@ def malpha(psi, alpha: int, method: str = "auto") -> float:
     if method == "auto":
         method = "direct" if N <= 6 else "xorfwht"
     return _load().sre_oracle_malpha(_ptr(a), N, int(alpha), 0 if method == "direct" else 1)
+
+
+# ---- TFIM with longitudinal field, Example 1 (Eq. (TFIM_LF_OBC)) ------------
+
+def tfim_hamiltonian(N: int, J: float = 1.0, hx: float = 1.5, hz: float = 1.5):
+    """Sparse H = -J sum_{i=0}^{N-2} Z_i Z_{i+1} - hx sum_i X_i - hz sum_i Z_i
+    on an open chain, qubit i <-> bit i of the basis index, Z|0> = |0>."""
+    import scipy.sparse as sp
+    d = 1 << N
+    t = np.arange(d, dtype=np.int64)
+    s = 1 - 2 * ((t[:, None] >> np.arange(N)) & 1)  # Z eigenvalue of each qubit
+    diag = -J * np.sum(s[:, :-1] * s[:, 1:], axis=1) - hz * np.sum(s, axis=1)
+    rows = [t] + [t] * N
+    cols = [t] + [t ^ (1 << i) for i in range(N)]
+    vals = [diag.astype(np.float64)] + [np.full(d, -hx, dtype=np.float64)] * N
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(d, d))
+
+
+def tfim_evolve(psi, dt: float, steps: int, J: float = 1.0, hx: float = 1.5, hz: float = 1.5):
+    """States after each of `steps` steps of exp(-i H dt) applied to psi,
+    by scipy.sparse.linalg.expm_multiply (the method the paper uses)."""
+    from scipy.sparse.linalg import expm_multiply
+    a = np.asarray(psi, dtype=np.complex128)
+    N = a.size.bit_length() - 1
+    H = tfim_hamiltonian(N, J, hx, hz)
+    out = []
+    for _ in range(steps):
+        a = expm_multiply(-1j * dt * H, a)
+        out.append(a.copy())
+    return out

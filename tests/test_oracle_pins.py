@@ -431,3 +431,46 @@ def test_malpha_planted_exponent_slip_is_caught(oracle_mod):
     assert abs(wrong_m - expect) > 1e-3
     right = np.sum(np.abs(table) ** 6)
     assert oracle_mod.malpha_from_sum(right, n2, 4, 3) == pytest.approx(expect, abs=1e-12)
+
+
+# ------------------------------------- TFIM quench reference (Example 1)
+
+def test_tfim_hamiltonian_matches_kronecker_terms(oracle_mod):
+    """H of Eq. (TFIM_LF_OBC) built term by term from 2x2 matrices (open
+    chain: bonds (i, i+1), i = 0..N-2) equals the oracle's sparse H."""
+    N, J, hx, hz = 4, 1.0, 1.5, 1.5
+    H = np.zeros((1 << N, 1 << N), dtype=np.complex128)
+    for i in range(N - 1):
+        H -= J * kron_list([PZ if j in (i, i + 1) else PI for j in range(N)])
+    for i in range(N):
+        H -= hx * kron_list([PX if j == i else PI for j in range(N)])
+        H -= hz * kron_list([PZ if j == i else PI for j in range(N)])
+    assert np.allclose(oracle_mod.tfim_hamiltonian(N, J, hx, hz).toarray(), H, atol=1e-14)
+
+
+def test_tfim_single_qubit_closed_form(oracle_mod):
+    """N = 1: H = -hx X - hz Z, so exp(-iHt) = cos(wt) I - i sin(wt) H / w with
+    w = sqrt(hx^2 + hz^2)."""
+    hx, hz, dt = 1.5, 1.5, 0.2
+    psi = np.array([0.6, 0.8j])
+    w = math.hypot(hx, hz)
+    H = -hx * PX - hz * PZ
+    states = oracle_mod.tfim_evolve(psi, dt, 3, 1.0, hx, hz)
+    for k, st in enumerate(states, start=1):
+        U = math.cos(w * k * dt) * PI - 1j * math.sin(w * k * dt) * H / w
+        assert np.allclose(st, U @ psi, atol=1e-13)
+
+
+def test_tfim_evolution_dense_and_conservation(oracle_mod):
+    """N = 5: equals the dense matrix exponential; norm and energy conserved."""
+    psi, _ = W.product_state(5, 12)
+    H = oracle_mod.tfim_hamiltonian(5)
+    states = oracle_mod.tfim_evolve(psi, 0.2, 4)
+    U = scipy.linalg.expm(-1j * 0.2 * H.toarray())
+    ref = psi.copy()
+    e0 = np.vdot(psi, H @ psi).real
+    for st in states:
+        ref = U @ ref
+        assert np.allclose(st, ref, atol=1e-12)
+        assert abs(np.linalg.norm(st) - 1) < 1e-12
+        assert abs(np.vdot(st, H @ st).real - e0) < 1e-10

@@ -249,6 +249,25 @@ SRE_API sre_status_t sre_brickwork_m2_series(sre_plan_t plan, int N, int S, int 
                                              void *d_states, sre_stream_t stream, double *d_m2_out);
 
 /*
+ * Hamiltonian quench dynamics (the paper's Example 1), evolved on the device:
+ * the transverse-field Ising chain with a longitudinal field, Eq.
+ * (TFIM_LF_OBC) on an open chain,
+ *     H = -J sum_{i=0}^{N-2} Z_i Z_{i+1} - hx sum_i X_i - hz sum_i Z_i
+ * (qubit i = bit i, Z|0> = |0>; the paper takes J = 1, hx = hz = 1.5).
+ * d_states (device, S * 2^N complex128, caller-owned) holds S initial states
+ * on entry; each of T steps applies exp(-i H dt) to every state (Chebyshev
+ * expansion to |J_k| < 1e-17, FP64) and then evaluates M2 of every state
+ * (batched path, in the plan's mode) into d_m2_out[t * S + s] (device, T * S
+ * doubles).  On return d_states holds the states at time T dt.  The plan's
+ * dtype must be SRE_C128; 1 <= N <= its N, 1 <= S <= 65535, T >= 1, dt >= 0
+ * and ||H|| dt <= 1000 with ||H|| <= |J|(N-1) + (|hx|+|hz|) N (SRE_EINVAL
+ * otherwise; SRE_EALIGN for misaligned pointers).  The plan keeps two
+ * evolution buffers of the states' size.  Asynchronous on `stream`.
+ */
+SRE_API sre_status_t sre_tfim_m2_series(sre_plan_t plan, int N, int S, int T, double dt, double J, double hx,
+                                        double hz, void *d_states, sre_stream_t stream, double *d_m2_out);
+
+/*
  * sre_sum4_range at Renyi order alpha: d_out[0] = sum over shifts
  * [x_begin, x_end) of sum_z |A_x(z)|^{2 alpha}, d_out[1] = n2; d_per_x as
  * there.  Asynchronous; shards add up to S_alpha.  SRE_EINVAL for alpha

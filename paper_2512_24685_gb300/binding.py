@@ -104,6 +104,8 @@ def _declare(lib):
         "sre_sum4_range": (S, [_vp, _vp, _i, _u64, _u64, _vp, _vp, _vp]),
         "sre_m_alpha": (S, [_vp, _vp, _i, _i, _vp, _dp]),
         "sre_brickwork_m2_series": (S, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
+        "sre_tfim_m2_series": (S, [_vp, _i, _i, _i, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, _vp, _vp, _vp]),
         "sre_sum_pow_range": (S, [_vp, _vp, _i, _i, _u64, _u64, _vp, _vp, _vp]),
         "sre_m2_batched": (S, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), _i, _vp, _vp]),
         "sre_selftest_wait_timeout": (S, [_u64, _vp]),
@@ -358,6 +360,24 @@ class Plan:
             self._h, N, S, T, ctypes.c_void_p(gates.data_ptr()), ctypes.c_void_p(states.data_ptr()),
             _stream_handle(stream), ctypes.c_void_p(out.data_ptr())), "sre_brickwork_m2_series")
         return out, states
+
+    def tfim_m2_series(self, states, T: int, dt: float = 0.2, J: float = 1.0, hx: float = 1.5,
+                       hz: float = 1.5, stream=None):
+        """sre_tfim_m2_series: M2 after each of T steps exp(-i H dt) of the
+        TFIM with longitudinal field, evolved on the device.  states: complex128
+        CUDA tensor (S, 2^N) of initial states, overwritten by the states at
+        time T dt.  Returns M2 as a (T, S) float64 CUDA tensor."""
+        torch = _torch()
+        if states.dtype != torch.complex128 or states.dim() != 2 or not states.is_contiguous():
+            raise ValueError("states must be a contiguous complex128 tensor of shape (S, 2^N)")
+        S = int(states.shape[0])
+        N = _n_of(int(states.shape[1]))
+        out = torch.empty((int(T), S), dtype=torch.float64, device=states.device)
+        _check(load_library().sre_tfim_m2_series(
+            self._h, N, S, int(T), float(dt), float(J), float(hx), float(hz),
+            ctypes.c_void_p(states.data_ptr()), _stream_handle(stream), ctypes.c_void_p(out.data_ptr())),
+            "sre_tfim_m2_series")
+        return out
 
     def m2_batched(self, states, out=None, stream=None):
         """sre_m2_batched: M2 of many device states of uneven N (float64 CUDA tensor)."""

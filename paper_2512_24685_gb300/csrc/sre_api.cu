@@ -3,9 +3,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <string>
 #include <vector>
@@ -50,8 +52,10 @@ struct sre_plan_s {
     bool has_tuned[SRE_MAX_QUBITS + 1] = {};
     void *tune_state = nullptr;                     // synthetic state for autotuning
     sre::LargeCfg batch_cfg[SRE_MAX_QUBITS + 1];    // configurations handed to batches
-    double *d_series = nullptr;                     // one step's M2 values (brickwork series)
+    double *d_series = nullptr;                     // one step's M2 values (time series)
     int d_series_cap = 0;
+    void *d_evolve = nullptr;                       // TFIM evolution buffers
+    size_t d_evolve_bytes = 0;
 };
 
 namespace {
@@ -207,6 +211,7 @@ sre_status_t sre_plan_destroy(sre_plan_t p) {
     cudaFree(p->d_stage);
     cudaFree(p->tune_state);
     cudaFree(p->d_series);
+    cudaFree(p->d_evolve);
     delete p;
     return SRE_OK;
 }
@@ -527,6 +532,46 @@ sre_status_t sre_brickwork_m2_series(sre_plan_t p, int N, int S, int T, const vo
         p->ws.launches += (unsigned long long)(N - 1);
         // every step's batch has the same states and output, so after the
         // first step the batched path replays its captured graph
+        sre_status_t s = sre_m2_batched(p, ptrs.data(), Ns.data(), S, stream, p->d_series);
+        if (s != SRE_OK) return s;
+        if ((e = cudaMemcpyAsync(d_m2_out + (size_t)t * S, p->d_series, sizeof(double) * (size_t)S,
+                                 cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    return SRE_OK;
+}
+
+sre_status_t sre_tfim_m2_series(sre_plan_t p, int N, int S, int T, double dt, double J, double hx, double hz,
+                                void *d_states, sre_stream_t stream, double *d_m2_out) {
+    if (!p || !d_states || !d_m2_out) return SRE_EINVAL;
+    if (p->dtype != SRE_C128 || N < 1 || N > p->N || S < 1 || S > 65535 || T < 1) return SRE_EINVAL;
+    const double a = std::fabs(J) * (N - 1) + (std::fabs(hx) + std::fabs(hz)) * N;
+    if (!(dt >= 0.0) || !std::isfinite(a) || !(a * dt <= 1000.0)) return SRE_EINVAL;
+    if (((uintptr_t)d_states) % 16 || ((uintptr_t)d_m2_out) % 8) return SRE_EALIGN;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (p->d_series_cap < S) {
+        cudaFree(p->d_series);
+        p->d_series = nullptr;
+        p->d_series_cap = 0;
+        if ((e = cudaMalloc(&p->d_series, sizeof(double) * (size_t)S)) != cudaSuccess) return cuda_fail(e);
+        p->d_series_cap = S;
+    }
+    const size_t one = ((size_t)S << N) * 16;
+    if (p->d_evolve_bytes < 2 * one) {
+        cudaFree(p->d_evolve);
+        p->d_evolve = nullptr;
+        p->d_evolve_bytes = 0;
+        if ((e = cudaMalloc(&p->d_evolve, 2 * one)) != cudaSuccess) return cuda_fail(e);
+        p->d_evolve_bytes = 2 * one;
+    }
+    std::vector<const void *> ptrs((size_t)S);
+    std::vector<int> Ns((size_t)S, N);
+    for (int s = 0; s < S; ++s) ptrs[s] = (const char *)d_states + ((size_t)s << N) * 16;
+    for (int t = 0; t < T; ++t) {
+        if ((e = sre::evolve_tfim_step(d_states, p->d_evolve, (char *)p->d_evolve + one, N, S, dt, J, hx, hz,
+                                       p->dev, st)) != cudaSuccess)
+            return cuda_fail(e);
         sre_status_t s = sre_m2_batched(p, ptrs.data(), Ns.data(), S, stream, p->d_series);
         if (s != SRE_OK) return s;
         if ((e = cudaMemcpyAsync(d_m2_out + (size_t)t * S, p->d_series, sizeof(double) * (size_t)S,

@@ -141,6 +141,10 @@ cudaError_t enqueue_convert(const void *src, sre_dtype_t from, void *dst, int N,
 cudaError_t evolve_init(void *d_states, int N, int S, const DeviceInfo &dev, cudaStream_t st);
 cudaError_t evolve_brickwork_step(void *d_states, int N, int S, int t, const void *d_gates,
                                   const DeviceInfo &dev, cudaStream_t st);
+// TFIM + longitudinal field: states <- exp(-i H dt) states (Chebyshev, FP64);
+// buf and acc are two more buffers of S * 2^N complex128.
+cudaError_t evolve_tfim_step(void *d_states, void *d_buf, void *d_acc, int N, int S, double dt, double J,
+                             double hx, double hz, const DeviceInfo &dev, cudaStream_t st);
 
 // Bounded-wait self test (see sre_selftest_wait_timeout).
 cudaError_t run_wait_selftest(long long wait_ns, cudaStream_t st, int *status_out);

@@ -427,6 +427,33 @@ def run_brickwork(binding, torch, W, cases=((14, 100, 20), (16, 100, 4))):
     return out
 
 
+def run_tfim(binding, torch, W, cases=((14, 100, 10), (16, 100, 3)), dt=0.2):
+    """Example 1's quench on the device: S random product states of N qubits
+    evolved by the TFIM with longitudinal field (J = 1, hx = hz = 1.5), T steps
+    of dt, M2 of every state after every step (sre_tfim_m2_series, FP32 M2 of
+    complex128 states)."""
+    import math
+    import numpy as np
+    out = {}
+    for N, S, T in cases:
+        psi0 = np.stack([W.product_state(N, W.config_seed(5, s))[0] for s in range(S)])
+        with binding.Plan(N, "c128", "fp32") as p:
+            warm = torch.from_numpy(psi0.copy()).cuda()
+            p.tfim_m2_series(warm, 1, dt)  # warm-up (first-step graph capture)
+            states = torch.from_numpy(psi0.copy()).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m2 = p.tfim_m2_series(states, T, dt)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+        out[f"N{N}"] = {"realizations": S, "steps": T, "dt": dt, "ms": ms, "ms_per_step": ms / T,
+                        "pauli_terms_per_s": S * T * 4.0 ** N / (ms / 1e3),
+                        "m2_first_step_mean": float(m2[0].double().mean()),
+                        "m2_last_step_mean": float(m2[-1].double().mean()),
+                        "haar_value": math.log2(2 ** N + 3) - 2}
+    return out
+
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the halved
 # two-pass launch, from one ncu capture of a 16384-shift slice at N = 20 in
 # the tuning below (0.379 GB read + 11.669 GB written), scaled by shifts to
@@ -614,6 +641,10 @@ def run_gpu(args):
             extras["brickwork_dynamics"] = run_brickwork(binding, torch, W)
         except Exception as exc:
             extras["brickwork_dynamics"] = {"error": repr(exc)}
+        try:
+            extras["tfim_quench"] = run_tfim(binding, torch, W)
+        except Exception as exc:
+            extras["tfim_quench"] = {"error": repr(exc)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -136,6 +136,16 @@ cudaError_t enqueue_batch_finalize(const Workspace &ws, const void *seg, const d
                                    cudaStream_t st);
 cudaError_t enqueue_convert(const void *src, sre_dtype_t from, void *dst, int N, cudaStream_t st);
 
+// Single-pass kernel (sre_mid.cu) for shift ranges whose transform spans one
+// or two 4096-entry blocks (N = 13; halved shifts of N = 14): one FP64
+// partial per shift in part[state * sps + shift index], also in per_x if
+// given (single state).
+bool mid_applies(int N, int half);
+template <typename R>
+cudaError_t launch_mid(int N, int half, const void *psi, const void *const *psis, int nstates, long long sps,
+                       uint64_t x_begin, int alpha, double *part, double *per_x, const DeviceInfo &dev,
+                       cudaStream_t st);
+
 // Brickwork circuit dynamics (sre_evolve.cu): S complex128 states of N
 // qubits set to |0...0>; one step t of even-bond then odd-bond gates.
 cudaError_t evolve_init(void *d_states, int N, int S, const DeviceInfo &dev, cudaStream_t st);

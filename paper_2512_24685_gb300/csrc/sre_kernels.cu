@@ -539,6 +539,18 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
             const uint64_t xb = half ? split : x_begin;
             const uint64_t xe = half ? x_end : split;
             if (xb >= xe) continue;
+            if (!tc_kind && mid_applies(N, half)) {
+                // one or two blocks per shift: single pass, one partial per shift
+                const long long ns = (long long)(xe - xb);
+                if (chunks + (size_t)ns > ws.chunk_cap) return cudaErrorInvalidValue;
+                if ((e = launch_mid<R>(N, half, psi, nullptr, 1, ns, xb, alpha, ws.chunk_sum + chunks,
+                                       d_per_x ? d_per_x + (xb - x_begin) : nullptr, dev, st)) != cudaSuccess)
+                    return e;
+                ws.launches += 1;
+                chunks += (size_t)ns;
+                if (!half) seg1 = (long long)chunks;
+                continue;
+            }
             LargeArgs a;
             int grid = 0;
             if ((e = make_large_args(&a, ws, dev, psi, N, xb, xe, half, eb, chunks,
@@ -740,6 +752,9 @@ BatchClass batch_class_layout(const DeviceInfo &dev, const Workspace &ws, int N,
     }
     L.cfg_full = choose_large_cfg(dev, N, eb, 0);
     L.cfg_half = tuned_half ? *tuned_half : choose_large_cfg(dev, N, eb, 1);
+    // ranges taken by the single-pass kernel have one partial per shift
+    if (mid_applies(N, 0)) L.cfg_full.C_log = 0;
+    if (mid_applies(N, 1)) L.cfg_half.C_log = 0;
     L.cps_full = (long long)(((uint64_t)kTile + (1ull << L.cfg_full.C_log) - 1) >> L.cfg_full.C_log);
     const uint64_t span = (1ull << N) - kTile;
     L.cps_half = (long long)((span + (1ull << L.cfg_half.C_log) - 1) >> L.cfg_half.C_log);
@@ -767,8 +782,17 @@ static cudaError_t enqueue_batch_class_t(const Workspace &ws, const DeviceInfo &
     for (int half = 0; half <= 1; ++half) {
         const LargeCfg &c = half ? L.cfg_half : L.cfg_full;
         const long long cps = half ? L.cps_half : L.cps_full;
-        if (!large_cfg_fits(ws, c, N, half)) return cudaErrorInvalidValue;
         const uint64_t xb = half ? (uint64_t)kTile : 0, xe = half ? (1ull << N) : (uint64_t)kTile;
+        if (mid_applies(N, half)) {
+            // cps = shifts per state (the layout gave this range one chunk per shift)
+            if ((e = launch_mid<R>(N, half, nullptr, d_ptrs, L.S, cps, xb, 2, parts + off, nullptr, dev, st)) !=
+                cudaSuccess)
+                return e;
+            ws.launches += 1;
+            off += (size_t)cps * L.S;
+            continue;
+        }
+        if (!large_cfg_fits(ws, c, N, half)) return cudaErrorInvalidValue;
         LargeArgs A;
         A.psi = nullptr;
         A.psis = d_ptrs;

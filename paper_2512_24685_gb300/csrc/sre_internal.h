@@ -15,7 +15,8 @@ constexpr int kPerThread = kTile / kThreads;  // 16 entries per thread (4 regist
 constexpr int kNormBlocks = 264;           // fixed grid of the norm reduction
 constexpr int kFinalThreads = 256;
 constexpr int kMaxRing = 64;                      // ring slots a tuned configuration may use
-constexpr size_t kTuneScratch = (size_t)96 << 20;  // scratch floor for N > 12 plans
+constexpr size_t kTuneScratch = (size_t)192 << 20;  // scratch floor for N > 12 plans (tuned rings)
+constexpr size_t kSlotScratch = (size_t)96 << 20;   // scratch floor for server slots (default rings)
 
 // Device-side result block of one evaluation (written by the finalize kernel).
 struct Result {
@@ -98,7 +99,7 @@ cudaError_t enqueue_fill_synthetic(void *buf, int N, sre_dtype_t dtype, cudaStre
 size_t workspace_scratch_bytes(const DeviceInfo &dev, int N_max, int elem_bytes, sre_mode_t mode);
 
 cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int elem_bytes,
-                            sre_mode_t mode);
+                            sre_mode_t mode, size_t scratch_floor = kTuneScratch);
 void workspace_free(Workspace *ws);
 
 // Enqueue the sum over shifts [x_begin, x_end) and the norm of one state.

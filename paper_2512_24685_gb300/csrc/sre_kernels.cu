@@ -295,7 +295,7 @@ void workspace_free(Workspace *ws) {
 }
 
 cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int elem_bytes,
-                            sre_mode_t mode) {
+                            sre_mode_t mode, size_t scratch_floor) {
     (void)mode;
     *ws = Workspace();
     ws->N_max = N_max;
@@ -319,8 +319,8 @@ cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int
     if (N_max > kTileBits) {
         // sizes for every N up to N_max and both halves of the shift range,
         // with room for tuned configurations: chunks of a single shift, up to
-        // kMaxRing ring slots, a scratch ring of at least kTuneScratch bytes
-        size_t scratch = kTuneScratch, item_cap = 0, chunk_cap = 0;
+        // kMaxRing ring slots, a scratch ring of at least scratch_floor bytes
+        size_t scratch = scratch_floor, item_cap = 0, chunk_cap = 0;
         for (int n = kTileBits + 1; n <= N_max; ++n) {
             for (int half = 0; half <= 1; ++half) {
                 const LargeCfg c = choose_large_cfg(dev, n, elem_bytes, half);

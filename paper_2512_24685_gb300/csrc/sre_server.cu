@@ -276,7 +276,7 @@ sre_status_t sre_server_create(const sre_server_cfg_t *cfg, sre_server_t *out) {
     s->slots.resize(cfg->max_inflight);
     for (Slot &sl : s->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = sre::workspace_alloc(&sl.ws, s->dev, cfg->max_N, eb, cfg->mode);
+        if (e == cudaSuccess) e = sre::workspace_alloc(&sl.ws, s->dev, cfg->max_N, eb, cfg->mode, sre::kSlotScratch);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_out, sizeof(double) * kBatchMaxCount);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, sizeof(double) * kBatchMaxCount);

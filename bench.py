@@ -456,13 +456,13 @@ def run_tfim(binding, torch, W, cases=((14, 100, 10), (16, 100, 3)), dt=0.2):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the halved
 # two-pass launch, from one ncu capture of a 16384-shift slice at N = 20 in
-# the tuning below (0.379 GB read + 11.669 GB written), scaled by shifts to
+# the tuning below (37.361 GB read + 58.768 GB written), scaled by shifts to
 # the 2^20 - 4096 halved shifts of one evaluation.  Valid only for that
 # kernel build and tuning; any other run reports null.
-TRAFFIC_SLICE_BYTES = 0.378755e9 + 11.668679e9
+TRAFFIC_SLICE_BYTES = 37.360901e9 + 58.768246e9
 TRAFFIC_SLICE_SHIFTS = 16384
-TRAFFIC_TUNING = {"x_batch_log": 0, "ring_slots": 23, "lag": 11, "pass2_tiles_log": 3,
-                  "pass1_blocks_log": 2, "pass1_staged": 1, "pass2_staged": 1}
+TRAFFIC_TUNING = {"x_batch_log": 2, "ring_slots": 11, "lag": 5, "pass2_tiles_log": 3,
+                  "pass1_blocks_log": 1, "pass1_staged": 1, "pass2_staged": 1}
 TRAFFIC_SOURCE = ("ncu --set full, 16384 halved shifts at N=20, scaled by shifts "
                   "to the halved launch (the x < 4096 launch adds < 1 %)")
 

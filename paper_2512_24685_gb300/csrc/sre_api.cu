@@ -294,7 +294,7 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
     if (!p || N < 1 || N > p->N) return SRE_EINVAL;
     if (N <= sre::kTileBits) return SRE_OK;
     // halved shifts taken by the single-pass kernel: nothing to tune
-    if (sre::mid_applies(N, 1) && !sre::tc_mode_available(p->mode)) return SRE_OK;
+    if (sre::mid_applies(N, 1, elem_bytes_for_mode(p->mode)) && !sre::tc_mode_available(p->mode)) return SRE_OK;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (!p->tune_state) {

@@ -137,11 +137,11 @@ cudaError_t enqueue_batch_finalize(const Workspace &ws, const void *seg, const d
                                    cudaStream_t st);
 cudaError_t enqueue_convert(const void *src, sre_dtype_t from, void *dst, int N, cudaStream_t st);
 
-// Single-pass kernel (sre_mid.cu) for shift ranges whose transform spans one
-// or two 4096-entry blocks (N = 13; halved shifts of N = 14): one FP64
-// partial per shift in part[state * sps + shift index], also in per_x if
-// given (single state).
-bool mid_applies(int N, int half);
+// Single-pass kernel (sre_mid.cu) for shift ranges whose transform spans one,
+// two or (FP32, elem_bytes 8) four 4096-entry blocks: one FP64 partial per
+// shift in part[state * sps + shift index], also in per_x if given (single
+// state).
+bool mid_applies(int N, int half, int elem_bytes);
 template <typename R>
 cudaError_t launch_mid(int N, int half, const void *psi, const void *const *psis, int nstates, long long sps,
                        uint64_t x_begin, int alpha, double *part, double *per_x, const DeviceInfo &dev,

@@ -539,7 +539,7 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
             const uint64_t xb = half ? split : x_begin;
             const uint64_t xe = half ? x_end : split;
             if (xb >= xe) continue;
-            if (!tc_kind && mid_applies(N, half)) {
+            if (!tc_kind && mid_applies(N, half, eb)) {
                 // one or two blocks per shift: single pass, one partial per shift
                 const long long ns = (long long)(xe - xb);
                 if (chunks + (size_t)ns > ws.chunk_cap) return cudaErrorInvalidValue;
@@ -753,8 +753,8 @@ BatchClass batch_class_layout(const DeviceInfo &dev, const Workspace &ws, int N,
     L.cfg_full = choose_large_cfg(dev, N, eb, 0);
     L.cfg_half = tuned_half ? *tuned_half : choose_large_cfg(dev, N, eb, 1);
     // ranges taken by the single-pass kernel have one partial per shift
-    if (mid_applies(N, 0)) L.cfg_full.C_log = 0;
-    if (mid_applies(N, 1)) L.cfg_half.C_log = 0;
+    if (mid_applies(N, 0, eb)) L.cfg_full.C_log = 0;
+    if (mid_applies(N, 1, eb)) L.cfg_half.C_log = 0;
     L.cps_full = (long long)(((uint64_t)kTile + (1ull << L.cfg_full.C_log) - 1) >> L.cfg_full.C_log);
     const uint64_t span = (1ull << N) - kTile;
     L.cps_half = (long long)((span + (1ull << L.cfg_half.C_log) - 1) >> L.cfg_half.C_log);
@@ -783,7 +783,7 @@ static cudaError_t enqueue_batch_class_t(const Workspace &ws, const DeviceInfo &
         const LargeCfg &c = half ? L.cfg_half : L.cfg_full;
         const long long cps = half ? L.cps_half : L.cps_full;
         const uint64_t xb = half ? (uint64_t)kTile : 0, xe = half ? (1ull << N) : (uint64_t)kTile;
-        if (mid_applies(N, half)) {
+        if (mid_applies(N, half, (int)sizeof(v2_t<R>))) {
             // cps = shifts per state (the layout gave this range one chunk per shift)
             if ((e = launch_mid<R>(N, half, nullptr, d_ptrs, L.S, cps, xb, 2, parts + off, nullptr, dev, st)) !=
                 cudaSuccess)

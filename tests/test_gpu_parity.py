@@ -105,7 +105,7 @@ def test_stabilizer_states_zero(sre, torch_cuda, N):
     assert abs(gpu_m2(sre, torch_cuda, psi, "fp64")) <= TOL["fp64"]
 
 
-@pytest.mark.parametrize("N", [13, 14])
+@pytest.mark.parametrize("N", [13, 14, 15])
 def test_per_shift_sums(sre, torch_cuda, N):
     """sum_z |A_x(z)|^4 for every shift x equals the oracle's Algorithm-1 loop."""
     psi = W.haar_state(N, 31 * N)

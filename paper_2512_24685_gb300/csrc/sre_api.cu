@@ -114,7 +114,7 @@ const char *sre_status_str(sre_status_t s) {
 
 const char *sre_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 
-int sre_version(void) { return 10000; }
+int sre_version(void) { return 10100; }
 
 sre_status_t sre_plan_create(int N, sre_dtype_t dtype, sre_plan_t *out) {
     if (!out || N < 1 || N > SRE_MAX_QUBITS) return SRE_EINVAL;

@@ -63,6 +63,9 @@ struct Workspace {
     Result *result = nullptr;      // device result block
     void *conv = nullptr;          // state converted to the compute type (lazy)
     size_t conv_bytes = 0;
+    int *tc_e = nullptr;           // tensor-core path: scale exponent per x >> 12
+    double *tc_bn = nullptr;       // tensor-core path: l2 norm per 4096-entry block
+    int tc_cap = 0;                // entries of tc_e / tc_bn
     // profiling: events recorded around the main transform kernel when set
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     mutable const char *main_kernel = "";
@@ -82,12 +85,15 @@ cudaError_t query_device(DeviceInfo *info);
 // shifts, x >= 4096).
 LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half);
 
-// Tensor-core launch of the halved two-pass kernel (sre_tc.cu): tc_kind 1 =
-// BF16 hi/lo split, 2 = FP16 hi/lo split; cudaErrorNotSupported if the
-// pass-2 bit count has no tensor-core instantiation.
+// Tensor-core two-pass kernel (sre_tc.cu) for the halved shifts of one
+// state: tc_kind 1 = BF16 hi/lo pieces, 2 = FP16 hi/lo pieces.  tc_applies
+// says whether it covers (N, half, Renyi order, state alignment); the launch
+// first computes the per-shift fixed-point scales of the state into
+// ws.tc_bn / ws.tc_e.
 struct LargeArgs;
-cudaError_t launch_large_tc(const LargeArgs &a, int grid, cudaStream_t st, int tc_kind);
-size_t tc_extra_smem_bytes();
+bool tc_applies(int N, int half, int alpha, const void *psi);
+cudaError_t launch_large_tc(const LargeArgs &a, const Workspace &ws, const DeviceInfo &dev, int grid,
+                            cudaStream_t st, int tc_kind);
 
 // Does a (possibly tuned) configuration fit the workspace allocation?
 bool large_cfg_fits(const Workspace &ws, const LargeCfg &c, int N, int half);

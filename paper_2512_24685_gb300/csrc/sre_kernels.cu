@@ -291,6 +291,8 @@ void workspace_free(Workspace *ws) {
     cudaFree(ws->status);
     cudaFree(ws->result);
     cudaFree(ws->conv);
+    cudaFree(ws->tc_e);
+    cudaFree(ws->tc_bn);
     *ws = Workspace();
 }
 
@@ -339,6 +341,9 @@ cudaError_t workspace_alloc(Workspace *ws, const DeviceInfo &dev, int N_max, int
         SRE_TRY(cudaMalloc(&ws->item_part, sizeof(double) * item_cap));
         SRE_TRY(cudaMalloc(&ws->chunk_sum, sizeof(double) * chunk_cap));
         SRE_TRY(cudaMalloc(&ws->counters, sizeof(unsigned) * 3 * chunk_cap));
+        ws->tc_cap = 1 << (N_max - kTileBits);
+        SRE_TRY(cudaMalloc(&ws->tc_e, sizeof(int) * ws->tc_cap));
+        SRE_TRY(cudaMalloc(&ws->tc_bn, sizeof(double) * ws->tc_cap));
     }
 #undef SRE_TRY
     return cudaSuccess;
@@ -420,7 +425,7 @@ cudaError_t encode_p2_tmap(LargeArgs &a) {
 
 template <typename R, int H2, bool HALF>
 static cudaError_t launch_large_h(const LargeArgs &a, int grid, cudaStream_t st) {
-    const size_t smem = large_smem_bytes<R, H2>(0);
+    const size_t smem = large_smem_bytes<R, H2>();
     auto kern = k_large<R, H2, HALF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -539,7 +544,8 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
             const uint64_t xb = half ? split : x_begin;
             const uint64_t xe = half ? x_end : split;
             if (xb >= xe) continue;
-            if (!tc_kind && mid_applies(N, half, eb)) {
+            const bool tc_here = tc_kind && tc_applies(N, half, alpha, psi);
+            if (!tc_here && mid_applies(N, half, eb)) {
                 // one or two blocks per shift: single pass, one partial per shift
                 const long long ns = (long long)(xe - xb);
                 if (chunks + (size_t)ns > ws.chunk_cap) return cudaErrorInvalidValue;
@@ -558,8 +564,8 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
                                      cfg_override && half ? cfg_override : nullptr, &grid)) != cudaSuccess)
                 return e;
             a.alpha = alpha;
-            if (half && tc_kind)
-                e = launch_large_tc(a, grid, st, tc_kind);
+            if (tc_here)
+                e = launch_large_tc(a, ws, dev, grid, st, tc_kind);
             else if (half)
                 e = launch_large<R, true>(a, grid, st);
             else

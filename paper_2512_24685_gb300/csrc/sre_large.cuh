@@ -1,13 +1,14 @@
-// sre_large.cuh -- the persistent two-pass kernel of libsre (N > 12),
-// shared by the CUDA-core translation unit and the tensor-core one.
+// sre_large.cuh -- the persistent two-pass CUDA-core kernel of libsre
+// (N > 12), and the work-item order and bounded waits it shares with the
+// tensor-core kernel of sre_tc.cu.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "sre_internal.h"
+#include "sre_async.cuh"
 #include "sre_stage.cuh"
-#include "sre_tc.cuh"
 #include "sre_tile.cuh"
 
 namespace sre {
@@ -49,9 +50,12 @@ using namespace dev;
 //
 // FP32 launches with 5 <= h2 <= 8 stage pass-2 tiles through TMA
 // (sre_stage.cuh): tmap then describes the scratch ring as a 2-D FP32 array
-// of 8192 columns (4096 complex per block t'_h) by R * C * 2^h2 rows.
+// of 8192 columns (4096 complex per block t'_h) by R * C * 2^h2 rows.  The
+// tensor-core kernel (sre_tc.cu) describes its 16-bit scratch planes there
+// instead and reads its per-shift fixed-point scales from tc_e.
 struct LargeArgs {
-    CUtensorMap tmap;          // pass-2 staging (encode_p2_tmap), else unused
+    CUtensorMap tmap;          // pass-2 staging (encode_p2_tmap / tc map), else unused
+    const int *tc_e;           // tensor-core kernel: scale exponent per x >> 12
     const void *psi;           // the state (single-state launch)
     const void *const *psis;   // or: states of one batch class (device array)
     long long chunks_per_state;  // chunks of each state (batch class)
@@ -132,28 +136,27 @@ __host__ __device__ constexpr bool large_uses_tma() {
 // Pass 1 of this instantiation can take its block pairs by bulk copy (FP32
 // CUDA-core path; used at run time for one shift per chunk and 16-byte
 // aligned states).
-template <typename R, int TC>
+template <typename R>
 __host__ __device__ constexpr bool large_stages_pass1() {
-    return sizeof(R) == 4 && TC == kTcNone;
+    return sizeof(R) == 4;
 }
 
 // Dynamic shared memory of k_large: three relayout buffers (the first two
-// double as the TMA stages of pass 2, hence 1024-byte alignment) and the
-// tensor-core extras.
+// double as the TMA stages of pass 2, hence 1024-byte alignment).
 template <typename R, int H2>
-__host__ __device__ constexpr size_t large_smem_bytes(size_t tc_extra) {
-    return (size_t)3 * kTileSlots * sizeof(v2_t<R>) + tc_extra + (large_uses_tma<R, H2>() ? 1024 : 0);
+__host__ __device__ constexpr size_t large_smem_bytes() {
+    return (size_t)3 * kTileSlots * sizeof(v2_t<R>) + (large_uses_tma<R, H2>() ? 1024 : 0);
 }
 
 // Host: encode LargeArgs::tmap for the launch's scratch ring.
 cudaError_t encode_p2_tmap(LargeArgs &a);
 
-template <typename R, int H2, bool HALF, int TC = kTcNone>
+template <typename R, int H2, bool HALF>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(const __grid_constant__ LargeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = v2_t<R>;
     constexpr bool kTma = large_uses_tma<R, H2>();
-    constexpr bool kStage1 = large_stages_pass1<R, TC>();
+    constexpr bool kStage1 = large_stages_pass1<R>();
     unsigned char *sbase = smem_raw;
     if constexpr (kTma) sbase += (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     V *bufB = reinterpret_cast<V *>(sbase);  // round 1 -> 2 moves, alternating with
@@ -167,25 +170,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
     unsigned tcount = 0;  // tiles that used a round 1 -> 2 move (uniform)
     uint32_t sphase = 0;  // parity of the next completion of each barrier
     uint32_t slost = 0;   // barriers whose completion wait expired
-
-    // tensor-core stage (TC != kTcNone, FP32 only): H_16 operand, mbarrier
-    // and TMEM after the three relayout buffers
-    TcState tc;
-    __shared__ uint32_t s_tmem;
-    if constexpr (TC != kTcNone) {
-        unsigned char *extra = reinterpret_cast<unsigned char *>(bufA + kTileSlots);
-        tc.b = extra;
-        tc.mbar = smem_u32(extra + kTcBBytes);
-        tc.phase = 0;
-        tc_init_h16<TC>(tc.b, threadIdx.x, kThreads);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (threadIdx.x == 0) mbar_init(tc.mbar, 1);
-        if (threadIdx.x < 32) tc_alloc(&s_tmem);
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        tc.tmem = s_tmem;
-    }
 
     const int tid = threadIdx.x;
     const int lgx = a.N - (HALF ? 1 : 0);        // log2 scratch entries per shift
@@ -338,20 +322,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
                     }
                     V *bB = (tcount & 1) ? bufC : bufB;
                     ++tcount;
-                    if constexpr (TC != kTcNone) {
-                        // bits 8-11 and 4-7 on CUDA cores, bits 0-3 as an MMA
-                        // with H_16; the A operand goes to the cross-warp
-                        // buffer this tile does not use (no one reads it now)
-                        reg_stages<2, 12, R>(v);
-                        relayout<2, 1, false, R>(v, bB, tid);
-                        reg_stages<1, 12, R>(v);
-                        relayout<1, 0, true, R>(v, bufA, tid);
-                        tc.a = reinterpret_cast<unsigned char *>(bB == bufB ? bufC : bufB);
-                        if (!tc_round0<TC>(v, tc, tid, a.wait_ns) && tid == 0)
-                            atomicCAS(a.status, 0, (int)SRE_ETIMEDOUT);
-                    } else {
-                        tile_fwht12_rev<R>(v, bufA, bB, tid);
-                    }
+                    tile_fwht12_rev<R>(v, bufA, bB, tid);
                     // output in round-0 layout (z_l = 16 tid + i) stored at the
                     // bit-permuted position i << 8 | tid: coalesced stores; pass 2
                     // only sums over z, so the order of z inside a block is free
@@ -521,12 +492,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
         // wait for it once more (bounded) before the CTA's memory is released
         for (int st = 0; st < 3; ++st)
             if (slost & (1u << st)) mbar_wait_bounded(smem_u32(&s_mbar[st]), ((sphase >> st) & 1u) ^ 1u, a.wait_ns);
-    }
-    if constexpr (TC != kTcNone) {
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (threadIdx.x < 32) tc_dealloc(tc.tmem);
     }
 }
 

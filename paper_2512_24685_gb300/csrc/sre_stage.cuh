@@ -34,7 +34,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "sre_tc.cuh"
+#include "sre_async.cuh"
 #include "sre_tile.cuh"
 
 namespace sre {
@@ -191,40 +191,6 @@ __device__ __forceinline__ float p2_tile(const unsigned char *stage, float2 *xbu
     reg_stages_mask<L::maskB(), float>(v);
     return sum_order<float, HALF>(v, alpha);
 }
-
-// ------------------------------------------------- TMA / mbarrier helpers
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-
-// 2-D tiled TMA load of the box at (x, y) of *tmap into shared memory at
-// dst, completing `bytes` of transaction count on mbar.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tmap, int x, int y,
-                                            uint32_t mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(mbar)
-        : "memory");
-}
-
-// 1-D bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned)
-// from global memory into shared memory at dst, completing on mbar.
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(mbar)
-        : "memory");
-}
-
-// Order this thread's earlier generic-proxy accesses (and those it has
-// observed through acquire / barrier) before its later async-proxy ones.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 }  // namespace dev
 }  // namespace sre

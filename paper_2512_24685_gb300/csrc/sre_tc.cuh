@@ -1,33 +1,31 @@
-// sre_tc.cuh -- tensor-core Hadamard stage (tcgen05, sm_100+/sm_103a).
+// sre_tc.cuh -- tcgen05 primitives and the fixed-point hi/lo split of the
+// tensor-core Hadamard stages (split-precision modes).
 //
-// One round of the tile transform -- the butterflies over four index bits,
-// i.e. a multiplication of each 16-entry row by H_16 = H_2^{(x)4} (the
-// recursion of the supplement's FWHT section) -- done as a dense MMA:
+// The supplement's FWHT section writes H_{2^N} = H_2^{(x)N} (block recursion),
+// so every group of index bits is transformed by an exact +-1 Hadamard
+// factor.  A stage over 7 bits is the dense product D = H_128 B, with H_128 in
+// tensor memory as the A operand and the data B in shared memory.
 //
-//   D[m][n] = sum_k A[m][k] H_16[n][k],   H_16[n][k] = (-1)^{popc(n & k)},
-//
-// with A = the thread rows of the tile in round-0 layout (thread tid owns
-// row tid: its 16 entries e = 16 tid + i), real and imaginary parts as
-// separate rows (4 M-blocks of 128 rows).  H_16 has exact +-1 entries, so
-// the only rounding is in representing A: each FP32 value v is split as
-// hi = round(v), lo = round(v - hi) in BF16 (or FP16, after a per-row power
-// of two scaling that keeps the row inside FP16's range), and the MMA
-// accumulates D = A_hi H + A_lo H in FP32 in tensor memory.
-//
-// Operands live in shared memory in the canonical no-swizzle K-major layout
-// of 8-row x 16-byte core matrices: element (row r, k) at byte
-//   (r / 8) * 256 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
-// so the descriptors use leading (K) byte offset 128 and stride (M/N) byte
-// offset 256.  One thread issues the 8 MMAs (M = 128, N = 16, K = 16) of a
-// tile and commits them to an mbarrier; every thread waits on it (bounded by
-// %globaltimer) and reads its two rows back from TMEM with tcgen05.ld
-// (warp w reaches lanes 32 (w % 4) .. + 31).
+// Fixed point.  The tensor cores accumulate in FP32 without round-to-nearest;
+// sums of integers below 2^24 are nevertheless exact.  So a block of FP32
+// values v that shares one power-of-two scale s is split as
+//   h  = rn(v s)            an integer with |h| <= 2^P,
+//   l  = rn_T(v s - h)      |l| <= 1/2, rounded to the piece type T,
+// with P = 8 for BF16 and P = 11 for FP16 (the integers a piece holds
+// exactly).  The two pieces form the two 64-column halves of one N = 128
+// operand, so the MMA accumulates H h and H l in separate TMEM columns: the
+// first sum is an exact integer (|sum| <= 2^(P+7)), the second only feels
+// truncation far below the result's own rounding.  The value is represented
+// to 2^-(2P+2) of the block maximum (18 bits for BF16, 24 for FP16).  The hi
+// piece is stored negated (-h comes out of the rounding for free), so a
+// result is lo - hi.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sre_async.cuh"
 #include "sre_tile.cuh"
 
 namespace sre {
@@ -35,40 +33,13 @@ namespace dev {
 
 enum TcKind { kTcNone = 0, kTcBf16 = 1, kTcFp16 = 2 };
 
-constexpr int kTcCols = 64;        // TMEM columns per CTA: 4 M-blocks x N = 16
-constexpr int kTcATileBytes = 4096;  // 128 rows x 16 x 2 bytes
-constexpr int kTcABytes = 8 * kTcATileBytes;  // 4 blocks x (hi, lo) = 32 KB
-constexpr int kTcBBytes = 512;      // H_16, 16 x 16 x 2 bytes
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// byte offset of element (r, k) of a K = 16 operand in the canonical layout
-__host__ __device__ constexpr int tc_off(int r, int k) {
-    return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
-}
-
-// tcgen05 shared-memory matrix descriptor, no swizzle, K-major
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
-    d |= (uint64_t)(128 >> 4) << 16;                  // leading (K) byte offset
-    d |= (uint64_t)(256 >> 4) << 32;                  // stride (M/N) byte offset
-    d |= (uint64_t)1 << 46;                           // descriptor version
-    return d;                                         // base offset 0, no swizzle
-}
-
-// instruction descriptor: kind::f16, F32 accumulate, A/B = BF16 or FP16,
-// both K-major, M = 128, N = 16
+// Integer bits held exactly by one piece (hi in [-2^P, 2^P]).
 template <int KIND>
-__host__ __device__ constexpr uint32_t tc_idesc() {
-    return (1u << 4)                                  // D format F32
-           | ((KIND == kTcBf16 ? 1u : 0u) << 7)       // A format
-           | ((KIND == kTcBf16 ? 1u : 0u) << 10)      // B format
-           | ((16u >> 3) << 17)                       // N / 8
-           | ((128u >> 4) << 24);                     // M / 16
+__host__ __device__ constexpr int tc_piece_bits() {
+    return KIND == kTcBf16 ? 8 : 11;
 }
+
+// ---------------------------------------------------------------- fences
 
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -77,192 +48,169 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// whole warp: allocate kTcCols TMEM columns, address written to *slot
-__device__ __forceinline__ void tc_alloc(uint32_t *slot) {
+// ---------------------------------------------------- tensor memory (TMEM)
+
+// Whole warp: allocate ncols (power of two >= 32) columns; address to *slot.
+__device__ __forceinline__ void tc_alloc(uint32_t *slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                 "r"(kTcCols)
+                 "r"(ncols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tc_dealloc(uint32_t taddr) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols) : "memory");
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
+// Whole warp: 8 consecutive 32-bit columns of this warp's 32 lanes.
+__device__ __forceinline__ void tc_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Whole warp: 16 consecutive 32-bit columns of this warp's 32 lanes (lane i
+// of the warp gets TMEM lane 32 (warp % 4) + i).  Complete after tc_wait_ld.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&u)[16]) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+        : "r"(taddr)
         : "memory");
 }
 
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------------- MMA
+
+// Shared-memory matrix descriptor (sm_100 format: start, leading and stride
+// byte offsets in 16-byte units, version 1, swizzle mode in bits 61-63).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t swizzle) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)swizzle << 61);
+}
+
+// B operand, N-major (N contiguous), no swizzle: core matrices of 8 K-rows x
+// 16 bytes; `kgroup` = byte stride between 8-row groups along K (leading
+// offset), `ngroup` = byte stride between 8-column groups along N (stride
+// offset).  These roles were established on GB300 with integer operands
+// (the other assignment gives wrong sums).
+__device__ __forceinline__ uint64_t tc_desc_mn(uint32_t saddr, uint32_t kgroup, uint32_t ngroup) {
+    return tc_desc(saddr, kgroup, ngroup, 0);
+}
+
+// B operand, N-major, 128-byte swizzle (the layout a TMA box of 128-byte rows
+// with CU_TENSOR_MAP_SWIZZLE_128B writes): atoms of 8 K-rows x 128 bytes,
+// 8-row groups 1024 bytes apart (stride offset), 64-element atom columns
+// `atom_col` bytes apart (leading offset).  Start address 1024-aligned.
+__device__ __forceinline__ uint64_t tc_desc_mn_sw128(uint32_t saddr, uint32_t atom_col) {
+    return tc_desc(saddr, atom_col, 1024, 2);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, A and B both BF16 or
+// both FP16, A K-major (from TMEM), B N-major, M = 128.
+template <int KIND>
+__host__ __device__ constexpr uint32_t tc_idesc(int N) {
+    return (1u << 4)                                  // D format F32
+           | ((KIND == kTcBf16 ? 1u : 0u) << 7)       // A format
+           | ((KIND == kTcBf16 ? 1u : 0u) << 10)      // B format
+           | (1u << 16)                               // B N-major
+           | ((uint32_t)(N >> 3) << 17)               // N / 8
+           | ((128u >> 4) << 24);                     // M / 16
+}
+
+// D[tmem d] (+)= A[tmem a] * B[smem desc]; issued by one thread.
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on mbar once every MMA this thread issued before has completed.
 __device__ __forceinline__ void tc_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                  : "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
+// ------------------------------------------------------ fixed-point split
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false on expiry.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long wait_ns) {
-    const unsigned long long t0 = globaltimer_ns();
-    for (unsigned it = 0; it < (1u << 28); ++it) {
-        if (mbar_try_wait(mbar, parity)) return true;
-        if ((it & 15) == 15 && (long long)(globaltimer_ns() - t0) > wait_ns) return false;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&r)[16]) {
-    uint32_t u[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
-          "=r"(u[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
-}
-
-// Split 16 values of one row into hi / lo halves and store them as rows
-// `row` of the hi and lo A tiles (canonical layout, two 16-byte chunks each).
+// Two FP32 values as one word of two pieces, a in the low half.
 template <int KIND>
-__device__ __forceinline__ void tc_store_row(const float (&x)[16], unsigned char *a_hi,
-                                             unsigned char *a_lo, int row) {
-    uint32_t hi[8], lo[8];
-#pragma unroll
-    for (int k = 0; k < 16; k += 2) {
-        if (KIND == kTcBf16) {
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(x[k]), h1 = __float2bfloat16_rn(x[k + 1]);
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(x[k] - __bfloat162float(h0));
-            const __nv_bfloat16 l1 = __float2bfloat16_rn(x[k + 1] - __bfloat162float(h1));
-            hi[k >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            lo[k >> 1] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-        } else {
-            const __half h0 = __float2half_rn(x[k]), h1 = __float2half_rn(x[k + 1]);
-            const __half l0 = __float2half_rn(x[k] - __half2float(h0));
-            const __half l1 = __float2half_rn(x[k + 1] - __half2float(h1));
-            hi[k >> 1] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-            lo[k >> 1] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        *reinterpret_cast<uint4 *>(a_hi + tc_off(row, 8 * c)) =
-            make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
-        *reinterpret_cast<uint4 *>(a_lo + tc_off(row, 8 * c)) =
-            make_uint4(lo[4 * c], lo[4 * c + 1], lo[4 * c + 2], lo[4 * c + 3]);
-    }
+__device__ __forceinline__ uint32_t tc_pack2(float a, float b) {
+    uint32_t d;
+    if (KIND == kTcBf16)
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    else
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
 }
 
-// Per-CTA state of the tensor stage.
-struct TcState {
-    unsigned char *a;     // kTcABytes of shared memory (A tiles)
-    unsigned char *b;     // kTcBBytes of shared memory (H_16)
-    uint32_t mbar;        // shared address of the mbarrier
-    uint32_t tmem;        // TMEM base address
-    uint32_t phase;       // parity of the next completion
-};
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23: x + M - M = rn(x) for |x| < 2^22
 
-// Write H_16 into b (all threads cooperate; caller synchronises).
+// Split the packed pair v (re, im) scaled by the packed pair s into the
+// negated integer piece (-rn(v s)) and the remainder piece; both words hold
+// (re, im) with re in the low half.
 template <int KIND>
-__device__ __forceinline__ void tc_init_h16(unsigned char *b, int tid, int nthreads) {
-    for (int idx = tid; idx < 256; idx += nthreads) {
-        const int n = idx >> 4, k = idx & 15;
-        const float h = (__popc(n & k) & 1) ? -1.f : 1.f;
-        unsigned short bits;
-        if (KIND == kTcBf16)
-            bits = __bfloat16_as_ushort(__float2bfloat16_rn(h));
-        else
-            bits = __half_as_ushort(__float2half_rn(h));
-        *reinterpret_cast<unsigned short *>(b + tc_off(n, k)) = bits;
-    }
+__device__ __forceinline__ void tc_split(unsigned long long v, unsigned long long s, unsigned long long magic,
+                                         uint32_t &hi_neg, uint32_t &lo) {
+    unsigned long long t, nh, r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(t) : "l"(v), "l"(s), "l"(magic));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(nh) : "l"(magic), "l"(t));  // -rn(v s), exact
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(v), "l"(s), "l"(nh));  // v s - rn(v s), exact
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(nh));
+    hi_neg = tc_pack2<KIND>(a, b);
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    lo = tc_pack2<KIND>(a, b);
 }
 
-// The tensor round: butterflies over tile bits 0-3 of a tile in round-0
-// layout (v[i] = entry 16 tid + i), in place.  All 256 threads call it.
-// Returns false if the bounded wait expired (v is then unreliable).
+// Power of two 2^(P - e) for a block maximum m = f 2^e (f in [1/2, 1)), so
+// that m 2^(P - e) < 2^P; 1 for m = 0; kept inside the normal FP32 range.
+template <int P>
+__device__ __forceinline__ float tc_block_scale(float m) {
+    if (!(m > 0.f)) return 1.f;
+    int e;
+    (void)frexpf(m, &e);
+    const int k = max(-126, min(126, P - e));
+    return __int_as_float((k + 127) << 23);
+}
+
+// Write the 128 x 128 A operand of a stage into TMEM columns [col, col + 64)
+// (two pieces per 32-bit column, k even in the low half): the Hadamard
+// matrix H_128[m][k] = (-1)^popc(m & k) for G = 7, or the block-diagonal
+// I_{2^(7-G)} (x) H_{2^G} for G < 7.  Warps 0-3 call it (warp w writes lanes
+// 32 w .. 32 w + 31); complete after tc_wait_st.
 template <int KIND>
-__device__ __forceinline__ bool tc_round0(cx_t<float> (&v)[16], TcState &tc, int tid, long long wait_ns) {
-    const int half_rows = tid >> 7;  // which 128-thread half: M-block 0/1 (re), 2/3 (im)
-    const int row = tid & 127;
-    float re[16], im[16];
+__device__ __forceinline__ void tc_write_hadamard(uint32_t tmem, int col, int G, int warp, int lane) {
+    const int m = 32 * warp + lane;
+    const int blk = ~((1 << G) - 1);
+    const unsigned short one = KIND == kTcBf16 ? 0x3F80 : 0x3C00;
+    const unsigned short neg = KIND == kTcBf16 ? 0xBF80 : 0xBC00;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) Cx<float>::unpack(v[i], re[i], im[i]);
-    float sre = 1.f, sim = 1.f;  // FP16: per-row power-of-two scale
-    if (KIND == kTcFp16) {
-        float mr = 0.f, mi = 0.f;
+    for (int c0 = 0; c0 < 64; c0 += 8) {
+        uint32_t r[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            mr = fmaxf(mr, fabsf(re[i]));
-            mi = fmaxf(mi, fabsf(im[i]));
+        for (int j = 0; j < 8; ++j) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 2 * (c0 + j) + h;
+                const unsigned short v =
+                    ((m & blk) != (k & blk)) ? (unsigned short)0 : ((__popc(m & k & ~blk) & 1) ? neg : one);
+                w |= (uint32_t)v << (16 * h);
+            }
+            r[j] = w;
         }
-        // scale so the row maximum lies in [2^10, 2^11): FP16 keeps ~2^-24 of it in hi + lo
-        int er = 0, ei = 0;
-        frexpf(mr, &er);
-        frexpf(mi, &ei);
-        sre = mr > 0.f ? ldexpf(1.f, 11 - er) : 1.f;
-        sim = mi > 0.f ? ldexpf(1.f, 11 - ei) : 1.f;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            re[i] *= sre;
-            im[i] *= sim;
-        }
+        tc_st8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(col + c0), r);
     }
-    unsigned char *blk_re = tc.a + (0 + half_rows) * 2 * kTcATileBytes;
-    unsigned char *blk_im = tc.a + (2 + half_rows) * 2 * kTcATileBytes;
-    tc_store_row<KIND>(re, blk_re, blk_re + kTcATileBytes, row);
-    tc_store_row<KIND>(im, blk_im, blk_im + kTcATileBytes, row);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-        tc_fence_after();
-        const uint64_t bdesc = tc_desc(smem_u32(tc.b));
-        constexpr uint32_t idesc = tc_idesc<KIND>();
-#pragma unroll
-        for (int blk = 0; blk < 4; ++blk) {
-            const uint32_t a_hi = smem_u32(tc.a + blk * 2 * kTcATileBytes);
-            const uint32_t d = tc.tmem + blk * 16;
-            tc_mma(d, tc_desc(a_hi), bdesc, idesc, 0u);
-            tc_mma(d, tc_desc(a_hi + kTcATileBytes), bdesc, idesc, 1u);
-        }
-        tc_commit(tc.mbar);
-    }
-    const bool ok = mbar_wait_bounded(tc.mbar, tc.phase, wait_ns);
-    tc.phase ^= 1u;
-    tc_fence_after();
-    const uint32_t lane_base = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
-    float dre[16], dim[16];
-    tc_ld16(tc.tmem + lane_base + (uint32_t)((0 + half_rows) * 16), dre);
-    tc_ld16(tc.tmem + lane_base + (uint32_t)((2 + half_rows) * 16), dim);
-    tc_fence_before();
-    const float ire = 1.f / sre, iim = 1.f / sim;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = Cx<float>::pack(dre[i] * ire, dim[i] * iim);
-    return ok;
 }
 
 }  // namespace dev

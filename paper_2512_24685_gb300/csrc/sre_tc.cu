@@ -12,9 +12,12 @@
 // pass 1, per 4096-entry block t'_h (a "tile", 8192 real values):
 //   * products conj(psi[t ^ x]) psi[t] in registers (thread tid holds
 //     t_l = i << 8 | tid, i < 16), butterflies over bits 8-11 in registers;
-//   * the tile maximum fixes a power-of-two scale; the values are split into
-//     fixed-point pieces and written as the N-major B operand [K = 128 rows
-//     t_l & 127] x [N = 128 columns (piece, t bit 7, i, re/im)];
+//   * a power-of-two scale: with FP16 pieces (24 bits), from the block
+//     pair's bound 16 max|psi| max|psi'| (every value is a signed sum of 16
+//     products); with BF16 pieces (18 bits), from the tile's own maximum;
+//     the values are split into fixed-point pieces and written
+//     as the N-major B operand [K = 128 rows t_l & 127] x [N = 128 columns
+//     (piece, t bit 7, i, re/im)];
 //   * one MMA stage D = H_128 B over bits 0-6 (8 MMAs, K = 16 each) into
 //     TMEM; the thread that reads lane z_l & 127 gets both t bit 7 columns
 //     and does the bit-7 butterfly in registers;
@@ -37,7 +40,7 @@
 // different blocks and needs one scale along K.  k_tc_scales computes E per
 // x >> 12 before the launch.
 //
-// Pipelining: warp-specialized roles (below) with two B buffers, two TMEM
+// Pipelining: warp-specialized roles (below) with two B buffers, three TMEM
 // accumulators and a ring of copy units, so that copies, MMAs and CUDA-core
 // work of different tiles overlap.
 #include <cuda.h>
@@ -116,18 +119,18 @@ __device__ __forceinline__ void tc_combine16(const uint32_t (&hv)[16], const uin
 // ---------------------------------------------------------------- kernel
 //
 // One CTA per SM, warp-specialized (448 threads):
-//   warps 0-7   compute: pass-1 products, bits 8-11, tile maximum, split into
-//               the B operand (double-buffered in shared memory); pass-2
-//               epilogue (warp w reads TMEM lanes 32 (w % 4) .., half of the
-//               columns): sum of fourth powers;
-//   warps 8-11  pass-1 epilogue: read an accumulator (warp 8 + q reads TMEM
-//               lanes 32 q .. 32 q + 31), bit-7 butterfly, split at the
-//               shift's scale, scratch stores;
+//   warps 0-7   compute: pass-1 products, bits 8-11, split into the B
+//               operand (double-buffered in shared memory) at the block
+//               pair's scale;
+//   warps 8-11  epilogue: read an accumulator (warp 8 + q reads TMEM lanes
+//               32 q .. 32 q + 31, all 128 columns); pass 1: bit-7
+//               butterfly, split at the shift's scale, scratch stores; pass
+//               2: sum of fourth powers;
 //   warp 12     producer: claims work items into a queue of kQueue entries;
 //               copies each pass-1 block pair (own and partner block of psi,
 //               32 KB each) or each pass-2 tile (hi and lo planes, TMA) into
 //               a ring of four 32 KB units;
-//   warp 13     MMA: D = A B for every tile into one of two TMEM
+//   warp 13     MMA: D = A B for every tile into one of three TMEM
 //               accumulators (128 columns each).
 // Every role walks the same item sequence; the handoffs are mbarriers:
 //   queue  q_full (producer -> 13 consumer warps), q_empty (13 arrivals);
@@ -135,8 +138,7 @@ __device__ __forceinline__ void tc_combine16(const uint32_t (&hv)[16], const uin
 //          u_empty (pass 1: compute warps after a block pair; pass 2: the
 //          MMA's commit);
 //   B      b_full (8 compute-warp arrivals), b_empty (MMA commit);
-//   D      d_full1 / d_full2 (MMA commit of a pass-1 / pass-2 tile),
-//          d_empty (4 arrivals from the group that read it).
+//   D      d_full (MMA commit), d_empty (4 epilogue-warp arrivals).
 // A parity wait only tells apart adjacent phases, so every barrier has one
 // group of waiters that sees each of its phases in order.  Each role waits
 // only on its own upstream for the same or an earlier item, or (pass-1
@@ -150,25 +152,40 @@ constexpr int kTcThreads = 448;
 constexpr int kCompWarps = 8, kEpiWarp0 = 8, kProdWarp = 12, kMmaWarp = 13;
 constexpr int kUnits = 4;                 // 32 KB ring units
 constexpr uint32_t kUnitBytes = 32768;
-constexpr int kQueue = 8;                 // item queue entries
-constexpr uint32_t kTcCols = 512;         // TMEM: H 64 | A2 64 | D0 128 | D1 128
+constexpr int kQueue = 2;                 // item queue entries (claims run at most this far ahead)
+constexpr int kAcc = 3;                   // TMEM accumulators
+constexpr uint32_t kTcCols = 512;         // TMEM: H 64 | A2 64 | D0 | D1 | D2 (128 each)
 constexpr uint32_t kBOff = kUnits * kUnitBytes;  // two B buffers after the units
 
+static_assert(128 + kAcc * 128 <= (int)kTcCols, "accumulators and factors fit TMEM");
 __host__ __device__ constexpr size_t tc_smem_bytes() {
     return (size_t)kUnits * kUnitBytes + 2 * (size_t)kUnitBytes + 1024;
 }
 
+// Item geometry shared by all roles.
+struct TcItem {
+    long long chunk;
+    int r, slot;
+    int pass1;
+    int E;             // scale exponent of the chunk's shifts
+    int first, count;  // valid shifts of the chunk: [first, first + count)
+    uint64_t xc, xh;
+    const float2 *psi;
+};
+
 struct __align__(8) TcShared {
     // "full" barriers exist once per consumer, so that every waiter sees
     // each phase of its barrier in order (a parity wait cannot tell a phase
-    // from the one two later): u_full1 / d_full1 for pass-1 block pairs and
-    // accumulators, u_full2 / d_full2 for pass-2 tiles
+    // from the one two later): u_full1 for pass-1 block pairs (compute
+    // warps), u_full2 for pass-2 tiles (MMA warp)
     uint64_t u_full1[kUnits], u_full2[kUnits], u_empty[kUnits];
-    uint64_t b_full[2], b_empty[2], d_full1[2], d_full2[2], d_empty[2];
+    uint64_t b_full[2], b_empty[2], d_full[kAcc], d_empty[kAcc];
     uint64_t q_full[kQueue], q_empty[kQueue];
     long long q_item[kQueue];
+    TcItem q_dec[kQueue];           // the item decoded once, by the producer
     unsigned long long s1_ring[8];  // pass-1 tile scale: (float bits, tile index + 1)
-    uint32_t maxv[2][kCompWarps];
+    uint32_t maxq[kCompWarps], maxp[kCompWarps];  // per block pair: max |psi|^2 of each warp's entries
+    uint32_t maxt[2][kCompWarps];                  // BF16: per tile, max |value| of each warp
     uint32_t tmem;
 };
 
@@ -191,19 +208,12 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, const La
 
 __device__ __forceinline__ void bar_sync_comp() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// Item geometry shared by all roles.
-struct TcItem {
-    long long chunk;
-    int r, slot;
-    bool pass1;
-    uint64_t xc, xh;
-    int E;
-    const float2 *psi;
-};
 
 __device__ __forceinline__ TcItem tc_item(const LargeArgs &a, long long item) {
     TcItem t;
-    decode_item(a, item, t.chunk, t.r, t.pass1);
+    bool p1;
+    decode_item(a, item, t.chunk, t.r, p1);
+    t.pass1 = p1 ? 1 : 0;
     t.slot = (int)(t.chunk % a.R);
     long long cl = t.chunk;
     t.psi = reinterpret_cast<const float2 *>(a.psi);
@@ -215,19 +225,17 @@ __device__ __forceinline__ TcItem tc_item(const LargeArgs &a, long long item) {
     t.xc = a.x0 + ((uint64_t)cl << a.C_log);
     t.xh = t.xc >> kTileBits;
     t.E = a.tc_e[t.xh];
+    const int C = 1 << a.C_log;
+    int f = 0;
+    while (f < C && !(t.xc + (uint64_t)f >= a.x_begin && t.xc + (uint64_t)f < a.x_end)) ++f;
+    int n = 0;
+    while (f + n < C && t.xc + (uint64_t)(f + n) >= a.x_begin && t.xc + (uint64_t)(f + n) < a.x_end) ++n;
+    t.first = f;
+    t.count = n;
     return t;
 }
 
 __device__ __forceinline__ bool x_valid(const LargeArgs &a, uint64_t x) { return x >= a.x_begin && x < a.x_end; }
-
-// Number of valid shifts of the chunk and the first one (they are contiguous).
-__device__ __forceinline__ void chunk_shifts(const LargeArgs &a, uint64_t xc, int &first, int &count) {
-    const int C = 1 << a.C_log;
-    first = 0;
-    while (first < C && !x_valid(a, xc + (uint64_t)first)) ++first;
-    count = 0;
-    while (first + count < C && x_valid(a, xc + (uint64_t)(first + count))) ++count;
-}
 
 // Block t_h of halved block index tp: a zero inserted at the pivot bit jh.
 __device__ __forceinline__ int tc_block(int tp, int jh) { return ((tp >> jh) << (jh + 1)) | (tp & ((1 << jh) - 1)); }
@@ -255,9 +263,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
         for (int k = 0; k < 2; ++k) {
             mbar_init(smem_u32(&sh.b_full[k]), kCompWarps);
             mbar_init(smem_u32(&sh.b_empty[k]), 1);
-            mbar_init(smem_u32(&sh.d_full1[k]), 1);
-            mbar_init(smem_u32(&sh.d_full2[k]), 1);
-            mbar_init(smem_u32(&sh.d_empty[k]), 4);
+        }
+        for (int k = 0; k < kAcc; ++k) {
+            mbar_init(smem_u32(&sh.d_full[k]), 1);
+            mbar_init(smem_u32(&sh.d_empty[k]), 4);  // the 4 epilogue warps
         }
         for (int k = 0; k < kQueue; ++k) {
             mbar_init(smem_u32(&sh.q_full[k]), 1);
@@ -293,10 +302,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                 long long item = (long long)atomicAdd(a.work, 1ull);
                 if (*(volatile int *)a.status != 0) item = a.n_items;  // stop: everyone drains
                 sh.q_item[qs] = item;
+                TcItem it{};
+                if (item < a.n_items) {
+                    it = tc_item(a, item);
+                    sh.q_dec[qs] = it;
+                }
                 mbar_arrive(smem_u32(&sh.q_full[qs]));
                 if (item >= a.n_items) break;
-                const TcItem it = tc_item(a, item);
-                int first, count;
+                int first = it.first, count = it.count;
                 auto take_unit = [&]() {
                     const int u = (int)(ucount % kUnits);
                     const unsigned long long use = ucount / kUnits;
@@ -305,7 +318,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                     return u;
                 };
                 if (it.pass1) {
-                    chunk_shifts(a, it.xc, first, count);
                     if (count == 0) continue;
                     const int jh = (63 - __clzll((long long)it.xc)) - kTileBits;
                     for (int kb = 0; kb < (1 << a.B1_log); ++kb) {
@@ -365,21 +377,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
         unsigned long long btile = 0;   // pass-1 tiles (B buffers, scale ring)
         unsigned long long dtile = 0;   // tiles of either pass (accumulators)
         uint32_t par_u = 0;             // parity of the next u_full1 (compute) / u_full2 (MMA) phase, per unit
-        uint32_t par_d = 0;             // parity of the next d_full1 (epilogue) / d_full2 (compute, MMA) phase
-        uint32_t par_d1m = 0;           // MMA: parity of the next d_full1 commit, per buffer
-        uint32_t mma_used1 = 0, mma_used2 = 0;  // MMA: buffers committed to d_full1 / d_full2
+        uint32_t par_d = 0;             // parity of the next d_full phase, per accumulator
+        uint32_t mma_used = 0;          // MMA: accumulators committed to
         float2 Q[16];                   // compute: own factors of the block pair
         for (long long k = 0;; ++k) {
             const int qs = (int)(k % kQueue);
             tc_wait(smem_u32(&sh.q_full[qs]), (uint32_t)((k / kQueue) & 1), a);
             const long long item = *(volatile long long *)&sh.q_item[qs];
+            TcItem it{};
+            if (item < a.n_items) it = sh.q_dec[qs];
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&sh.q_empty[qs]));
             if (item >= a.n_items) break;
-            const TcItem it = tc_item(a, item);
             if (it.pass1) {
-                int first, count;
-                chunk_shifts(a, it.xc, first, count);
+                const int first = it.first, count = it.count;
                 if (count == 0) {
                     if (is_epi) {
                         __threadfence();
@@ -404,8 +415,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                         ucount += 2;
                         const float2 *sq = reinterpret_cast<const float2 *>(sbase + (size_t)uq * kUnitBytes);
                         const float2 *sp = reinterpret_cast<const float2 *>(sbase + (size_t)up * kUnitBytes);
+                        // scale of the block pair: every value after the 4 register
+                        // butterflies is a signed sum of 16 products, so
+                        // |v| <= 16 max|phi_t| max|phi_t'| over the two blocks
+                        float mq = 0.f, mp = 0.f;
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) Q[i] = sq[(i << 8) | tid];
+                        for (int i = 0; i < 16; ++i) {
+                            Q[i] = sq[(i << 8) | tid];
+                            const float2 pn = sp[(i << 8) | tid];
+                            mq = fmaxf(mq, Q[i].x * Q[i].x + Q[i].y * Q[i].y);
+                            mp = fmaxf(mp, pn.x * pn.x + pn.y * pn.y);
+                        }
+                        {
+                            const uint32_t wq = __reduce_max_sync(0xffffffffu, __float_as_uint(mq));
+                            const uint32_t wp = __reduce_max_sync(0xffffffffu, __float_as_uint(mp));
+                            if (lane == 0) {
+                                sh.maxq[warp] = wq;
+                                sh.maxp[warp] = wp;
+                            }
+                        }
+                        bar_sync_comp();
+                        float s1_pair;  // FP16 pieces (24 bits) take the block pair's bound
+                        {
+                            uint32_t tq = sh.maxq[0], tpp = sh.maxp[0];
+#pragma unroll
+                            for (int w = 1; w < kCompWarps; ++w) {
+                                tq = max(tq, sh.maxq[w]);
+                                tpp = max(tpp, sh.maxp[w]);
+                            }
+                            // 1 + 2^-10 covers the rounding of the FP32 products and sums
+                            const float bound = 16.f * sqrtf(__uint_as_float(tq) * __uint_as_float(tpp)) * 1.0009765625f;
+                            s1_pair = tc_block_scale<P>(bound);
+                        }
                         for (int xl = first; xl < first + count; ++xl) {
                             const int xlow = xl0 + xl;
                             const int q = xlow >> 8, pl = tid ^ (xlow & 255);
@@ -416,23 +457,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                                 v[i] = conj_mul<float>(b.x, b.y, Q[i].x, Q[i].y);  // conj(phi_{t^x}) phi_t
                             }
                             reg_stages<2, 12, float>(v);  // bits 8-11
-                            // tile maximum -> power-of-two scale (non-negative
-                            // floats order like their bit patterns)
-                            float mx = 0.f;
+                            float s1 = s1_pair;
+                            if constexpr (KIND == kTcBf16) {
+                                // BF16 pieces hold 18 bits: scale by the tile's own
+                                // maximum (non-negative floats order like their bits)
+                                float m16[16];
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                float re, im;
-                                Cx<float>::unpack(v[i], re, im);
-                                mx = fmaxf(mx, fmaxf(fabsf(re), fabsf(im)));
+                                for (int i = 0; i < 16; ++i) {
+                                    float re, im;
+                                    Cx<float>::unpack(v[i], re, im);
+                                    m16[i] = fmaxf(fabsf(re), fabsf(im));
+                                }
+#pragma unroll
+                                for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+                                    for (int i = 0; i < w; ++i) m16[i] = fmaxf(m16[i], m16[i + w]);
+                                const int par = (int)(btile & 1);
+                                const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m16[0]));
+                                if (lane == 0) sh.maxt[par][warp] = wm;
+                                bar_sync_comp();
+                                uint32_t tm = sh.maxt[par][0];
+#pragma unroll
+                                for (int w = 1; w < kCompWarps; ++w) tm = max(tm, sh.maxt[par][w]);
+                                s1 = tc_block_scale<P>(__uint_as_float(tm));
                             }
-                            const int par = (int)(btile & 1);
-                            const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-                            if (lane == 0) sh.maxv[par][warp] = wm;
-                            bar_sync_comp();
-                            uint32_t tm = sh.maxv[par][0];
-#pragma unroll
-                            for (int w = 1; w < kCompWarps; ++w) tm = max(tm, sh.maxv[par][w]);
-                            const float s1 = tc_block_scale<P>(__uint_as_float(tm));
                             if (tid == 0) {
                                 const unsigned long long e =
                                     (unsigned long long)__float_as_uint(s1) | ((btile + 1) << 32);
@@ -477,22 +525,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                     for (int kb = 0; kb < nb; ++kb) {
                         ucount += 2;
                         for (int xl = 0; xl < count; ++xl) {
-                            const int bb = (int)(btile & 1), dd = (int)(dtile & 1);
+                            const int bb = (int)(btile & 1), dd = (int)(dtile % kAcc);
                             tc_wait(smem_u32(&sh.b_full[bb]), (uint32_t)((btile / 2) & 1), a);
-                            if (dtile >= 2) tc_wait(smem_u32(&sh.d_empty[dd]), (uint32_t)((dtile / 2 - 1) & 1), a);
+                            if (dtile >= kAcc) tc_wait(smem_u32(&sh.d_empty[dd]), (uint32_t)((dtile / kAcc - 1) & 1), a);
                             tc_fence_after();
                             if (lane == 0) {
-                                const uint32_t bsm = s0 + kBOff + (uint32_t)bb * kUnitBytes;
-                                const uint32_t d = tmem + 128u + 128u * (uint32_t)dd;
-#pragma unroll
-                                for (int s = 0; s < 8; ++s)
-                                    tc_mma_ts(d, tH + 8u * s, tc_desc_mn(bsm + 4096u * s, 2048u, 128u), idesc, s ? 1u : 0u);
+                                // K step s: operand rows 16 s .., 4096 bytes further
+                                tc_mma_stage(tmem + 128u * (uint32_t)(dd + 1), tH,
+                                             tc_desc_mn(s0 + kBOff + (uint32_t)bb * kUnitBytes, 2048u, 128u),
+                                             4096u >> 4, idesc);
                                 tc_commit(smem_u32(&sh.b_empty[bb]));
-                                tc_commit(smem_u32(&sh.d_full1[dd]));
+                                tc_commit(smem_u32(&sh.d_full[dd]));
                             }
                             __syncwarp();
-                            par_d1m ^= 1u << dd;
-                            mma_used1 |= 1u << dd;
+                            par_d ^= 1u << dd;
+                            mma_used |= 1u << dd;
                             ++btile;
                             ++dtile;
                         }
@@ -510,7 +557,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                         ucount += 2;
                         const int tp = (it.r << a.B1_log) + kb;
                         for (int xl = first; xl < first + count; ++xl) {
-                            const int dd = (int)(dtile & 1);
+                            const int dd = (int)(dtile % kAcc);
                             // this tile's scale (written before its operand)
                             float s1 = 1.f;
                             {
@@ -528,7 +575,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                                         break;
                                 }
                             }
-                            tc_wait(smem_u32(&sh.d_full1[dd]), (par_d >> dd) & 1u, a);
+                            tc_wait(smem_u32(&sh.d_full[dd]), (par_d >> dd) & 1u, a);
                             par_d ^= 1u << dd;
                             tc_fence_after();
                             const int k12 = P - it.E - ((__float_as_int(s1) >> 23) - 127);
@@ -536,7 +583,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                             const unsigned long long sc = pack2f(c12, c12);
                             const size_t row_hi = ((slot_row + 2 * (size_t)xl) << H2) + (size_t)tp;
                             const size_t row_lo = row_hi + ((size_t)1 << H2);
-                            const uint32_t dcol = tmem + 128u + 128u * (uint32_t)dd + ((uint32_t)(32 * qd) << 16);
+                            const uint32_t dcol = tmem + 128u * (uint32_t)(dd + 1) + ((uint32_t)(32 * qd) << 16);
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 // complex i = 8 h + j: hi columns (t bit 7 = b) 32 b + 16 h + 2 j (+1), lo 64 further
@@ -605,58 +652,60 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                 const int ntiles = valid ? 1 << a.G2_log : 0;
                 if (is_mma) {
                     for (int g = 0; g < ntiles; ++g) {
-                        const int u = (int)(ucount % kUnits), dd = (int)(dtile & 1);
+                        const int u = (int)(ucount % kUnits), dd = (int)(dtile % kAcc);
                         tc_wait(smem_u32(&sh.u_full2[u]), (par_u >> u) & 1u, a);
                         par_u ^= 1u << u;
-                        if (dtile >= 2) tc_wait(smem_u32(&sh.d_empty[dd]), (uint32_t)((dtile / 2 - 1) & 1), a);
+                        if (dtile >= kAcc) tc_wait(smem_u32(&sh.d_empty[dd]), (uint32_t)((dtile / kAcc - 1) & 1), a);
                         tc_fence_after();
                         if (lane == 0) {
-                            const uint32_t bsm = s0 + (uint32_t)u * kUnitBytes;
-                            const uint32_t d = tmem + 128u + 128u * (uint32_t)dd;
-#pragma unroll
-                            for (int s = 0; s < 8; ++s)
-                                tc_mma_ts(d, tA2 + 8u * s, tc_desc_mn_sw128(bsm + 2048u * s, 16384u), idesc, s ? 1u : 0u);
+                            // K step s: 16 swizzled rows, 2048 bytes further
+                            tc_mma_stage(tmem + 128u * (uint32_t)(dd + 1), tA2,
+                                         tc_desc_mn_sw128(s0 + (uint32_t)u * kUnitBytes, 16384u), 2048u >> 4, idesc);
                             tc_commit(smem_u32(&sh.u_empty[u]));
-                            tc_commit(smem_u32(&sh.d_full2[dd]));
+                            tc_commit(smem_u32(&sh.d_full[dd]));
                         }
                         __syncwarp();
                         par_d ^= 1u << dd;
-                        mma_used2 |= 1u << dd;
+                        mma_used |= 1u << dd;
                         ++ucount;
                         ++dtile;
                     }
-                } else if (is_comp) {
-                    // pass-2 epilogue: compute warp w reads TMEM lanes 32 (w % 4) ..,
-                    // hi columns 32 (w / 4) .. + 31 and the lo columns 64 further
-                    const int qd = warp & 3, ch = warp >> 2;
+                } else if (is_epi) {
+                    // pass-2 epilogue: warp 8 + q reads TMEM lanes 32 q .., all
+                    // 128 columns (hi 0-63, lo 64-127) in two halves
+                    const int qd = warp - kEpiWarp0;
                     float part = 0.f;
                     for (int g = 0; g < ntiles; ++g) {
-                        const int dd = (int)(dtile & 1);
-                        tc_wait(smem_u32(&sh.d_full2[dd]), (par_d >> dd) & 1u, a);
+                        const int dd = (int)(dtile % kAcc);
+                        tc_wait(smem_u32(&sh.d_full[dd]), (par_d >> dd) & 1u, a);
                         par_d ^= 1u << dd;
                         tc_fence_after();
-                        const uint32_t dcol =
-                            tmem + 128u + 128u * (uint32_t)dd + ((uint32_t)(32 * qd) << 16) + 32u * (uint32_t)ch;
-                        unsigned long long F[16];
-                        {
-                            uint32_t h0[16], h1[16], l0[16], l1[16];
-                            tc_ld16(dcol, h0);
-                            tc_ld16(dcol + 16u, h1);
-                            tc_ld16(dcol + 64u, l0);
-                            tc_ld16(dcol + 80u, l1);
-                            tc_wait_ld();
-                            tc_combine16(h0, l0, F);
-                            tc_combine16(h1, l1, F + 8);
-                        }
-                        // every compute warp has read the accumulator: release it
-                        tc_fence_before();
-                        bar_sync_comp();
-                        if (tid == 0) mbar_arrive_cnt(smem_u32(&sh.d_empty[dd]), 4);
+                        const uint32_t dcol = tmem + 128u * (uint32_t)(dd + 1) + ((uint32_t)(32 * qd) << 16);
                         unsigned long long s4 = 0ull;
 #pragma unroll
-                        for (int uu = 0; uu < 16; ++uu) {
-                            const unsigned long long sq = Cx<float>::mul(F[uu], F[uu]);
-                            s4 = Cx<float>::fma(sq, sq, s4);
+                        for (int h = 0; h < 2; ++h) {
+                            unsigned long long F[16];
+                            {
+                                uint32_t h0[16], h1[16], l0[16], l1[16];
+                                tc_ld16(dcol + 32u * h, h0);
+                                tc_ld16(dcol + 32u * h + 16u, h1);
+                                tc_ld16(dcol + 64u + 32u * h, l0);
+                                tc_ld16(dcol + 64u + 32u * h + 16u, l1);
+                                tc_wait_ld();
+                                tc_combine16(h0, l0, F);
+                                tc_combine16(h1, l1, F + 8);
+                            }
+                            if (h == 1) {
+                                // the accumulator has been read: release it
+                                tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(smem_u32(&sh.d_empty[dd]));
+                            }
+#pragma unroll
+                            for (int uu = 0; uu < 16; ++uu) {
+                                const unsigned long long sq = Cx<float>::mul(F[uu], F[uu]);
+                                s4 = Cx<float>::fma(sq, sq, s4);
+                            }
                         }
                         float sa, sb;
                         Cx<float>::unpack(s4, sa, sb);
@@ -671,7 +720,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                             const int zb0 = (j & ((1 << ipx_log) - 1)) << a.G2_log;
                             const size_t y_hi = (((size_t)it.slot * C + xl) * 2) << H2;
                             const int lines = (1 << a.G2_log) * 256;
-                            for (int L = tid; L < lines; L += 256) {
+                            for (int L = tid - kEpiWarp0 * 32; L < lines; L += 128) {
                                 const int g = L >> 8, w = L & 255;
                                 const int plane = w >> 7, b = (w & 127) >> H2, row = w & ((1 << H2) - 1);
                                 const int col = ((zb0 + g) * kBlocksPerTile + b) * 64;
@@ -685,20 +734,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
                     int last = 0;
                     if (lane == 0) {
-                        a.item_part[(((size_t)it.slot * a.P2 + j) * kCompWarps) + warp] = acc;
+                        a.item_part[(((size_t)it.slot * a.P2 + j) * 4) + qd] = acc;
                         __threadfence();
                         const unsigned old = atomicAdd(a.done2 + it.chunk, 1u);
-                        last = (old == (unsigned)(a.P2 * kCompWarps) - 1u);
+                        last = (old == (unsigned)(a.P2 * 4) - 1u);
                     }
                     last = __shfl_sync(0xffffffffu, last, 0);
                     if (last) {
                         // last warp of the chunk: per-shift and chunk
                         // sums in fixed order, then release the slot
                         __threadfence();
-                        const int per_x_items = (1 << ipx_log) * kCompWarps;
+                        const int per_x_items = (1 << ipx_log) * 4;
                         double cs = 0.0;
                         for (int qq = 0; qq < C; ++qq) {
-                            const double *ip = a.item_part + ((size_t)it.slot * a.P2 + ((size_t)qq << ipx_log)) * kCompWarps;
+                            const double *ip = a.item_part + ((size_t)it.slot * a.P2 + ((size_t)qq << ipx_log)) * 4;
                             double sx = 0.0;
                             for (int kk = lane; kk < per_x_items; kk += 32) sx += __ldcg(ip + kk);
 #pragma unroll
@@ -722,11 +771,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
         // the MMA warp: its last accumulators of either kind are complete
         // before exit (the latest phase of each used barrier)
         if (is_mma) {
-            for (int d = 0; d < 2; ++d) {
-                if (mma_used1 & (1u << d))
-                    mbar_wait_bounded(smem_u32(&sh.d_full1[d]), ((par_d1m >> d) & 1u) ^ 1u, a.wait_ns);
-                if (mma_used2 & (1u << d))
-                    mbar_wait_bounded(smem_u32(&sh.d_full2[d]), ((par_d >> d) & 1u) ^ 1u, a.wait_ns);
+            for (int d = 0; d < kAcc; ++d) {
+                if (mma_used & (1u << d))
+                    mbar_wait_bounded(smem_u32(&sh.d_full[d]), ((par_d >> d) & 1u) ^ 1u, a.wait_ns);
             }
         }
     }

@@ -134,6 +134,30 @@ __device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint
         : "memory");
 }
 
+// One Hadamard stage of a tile: eight MMAs (K = 16 each, 128 in all) into
+// the accumulator d, A from TMEM columns a0 + 8 s, B from the descriptor
+// b0 advanced by bstep (in 16-byte units) per K step; the first MMA
+// overwrites d.  One asm block, so that the eight issue back to back.
+__device__ __forceinline__ void tc_mma_stage(uint32_t d, uint32_t a0, uint64_t b0, uint32_t bstep, uint32_t idesc) {
+    const uint64_t s = bstep;
+    asm volatile(
+        "{\n\t.reg .pred p0, p1;\n\t"
+        "setp.ne.b32 p0, %18, %18;\n\t"
+        "setp.eq.b32 p1, %18, %18;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %9, %17, p0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], %10, %17, p1;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%3], %11, %17, p1;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%4], %12, %17, p1;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%5], %13, %17, p1;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%6], %14, %17, p1;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%7], %15, %17, p1;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%8], %16, %17, p1;\n\t}\n" ::"r"(d),
+        "r"(a0), "r"(a0 + 8u), "r"(a0 + 16u), "r"(a0 + 24u), "r"(a0 + 32u), "r"(a0 + 40u), "r"(a0 + 48u),
+        "r"(a0 + 56u), "l"(b0), "l"(b0 + s), "l"(b0 + 2 * s), "l"(b0 + 3 * s), "l"(b0 + 4 * s),
+        "l"(b0 + 5 * s), "l"(b0 + 6 * s), "l"(b0 + 7 * s), "r"(idesc), "r"(0)
+        : "memory");
+}
+
 // Arrive on mbar once every MMA this thread issued before has completed.
 __device__ __forceinline__ void tc_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)

@@ -208,6 +208,11 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, const La
 
 __device__ __forceinline__ void bar_sync_comp() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+// Release / acquire at GPU scope by one lane for its warp: after __syncwarp
+// the fence also orders the other lanes' earlier accesses (fences are
+// cumulative), so one lane does it instead of every lane.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 
 __device__ __forceinline__ TcItem tc_item(const LargeArgs &a, long long item) {
     TcItem t;
@@ -393,9 +398,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                 const int first = it.first, count = it.count;
                 if (count == 0) {
                     if (is_epi) {
-                        __threadfence();
                         __syncwarp();
-                        if (lane == 0) atomicAdd(a.done1 + it.chunk, 1u);
+                        if (lane == 0) {
+                            fence_acq_rel_gpu();
+                            atomicAdd(a.done1 + it.chunk, 1u);
+                        }
                     }
                     continue;
                 }
@@ -634,9 +641,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                         }
                     }
                     // the item's stores are complete: one arrival per epilogue warp
-                    __threadfence();
                     __syncwarp();
-                    if (lane == 0) atomicAdd(a.done1 + it.chunk, 1u);
+                    if (lane == 0) {
+                        fence_acq_rel_gpu();
+                        atomicAdd(a.done1 + it.chunk, 1u);
+                    }
                 } else {
                     // other lanes of the producer warp never get here; the
                     // count keeps the ring position of idle roles consistent
@@ -733,9 +742,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
                     int last = 0;
+                    __syncwarp();  // the warp's discards precede its arrival
                     if (lane == 0) {
                         a.item_part[(((size_t)it.slot * a.P2 + j) * 4) + qd] = acc;
-                        __threadfence();
+                        fence_acq_rel_gpu();
                         const unsigned old = atomicAdd(a.done2 + it.chunk, 1u);
                         last = (old == (unsigned)(a.P2 * 4) - 1u);
                     }
@@ -743,7 +753,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                     if (last) {
                         // last warp of the chunk: per-shift and chunk
                         // sums in fixed order, then release the slot
-                        __threadfence();
+                        fence_acq_rel_gpu();
                         const int per_x_items = (1 << ipx_log) * 4;
                         double cs = 0.0;
                         for (int qq = 0; qq < C; ++qq) {
@@ -758,7 +768,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                         }
                         if (lane == 0) {
                             a.chunk_sum[it.chunk] = cs;
-                            __threadfence();
+                            fence_acq_rel_gpu();
                             atomicExch(a.freed + it.chunk, 1u);
                         }
                     }

@@ -1,9 +1,12 @@
 #!/usr/bin/env python3
 """Benchmark: Pauli terms/s of the exact XOR-FWHT M2 at N = 20 on GB300.
 
-One step = one full M2 evaluation of an N = 20 Haar-random state (complex64,
-FP32 path): all 4^20 = 1.1e12 Pauli strings X^x Z^z, i.e. every row of the
-hot path (norm, XOR-shifted products, FWHT, |A|^4 reduction, FP64 sum, log2).
+One step = one full M2 evaluation of an N = 20 Haar-random state (complex64;
+by default the FP16 hi/lo split mode, whose Hadamard stages run on the
+tensor cores, --mode fp32 for the CUDA-core path): all 4^20 = 1.1e12 Pauli
+strings X^x Z^z, i.e. every row of the hot path (norm, XOR-shifted
+products, FWHT, |A|^4 reduction, FP64 sum, log2), |dM2| against the FP64
+oracle's value of the same state reported beside it.
 The state is resident in HBM before the timed region; the L2 is flushed
 (a 512 MiB write) between timed steps, outside the per-step CUDA events.
 
@@ -44,7 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--N", type=int, default=N_QUBITS)
-    ap.add_argument("--mode", default="fp32")
+    ap.add_argument("--mode", default="fp16_split",
+                    help="fp16_split (tensor cores, the fastest within the tolerance), bf16_split, fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
@@ -487,22 +491,30 @@ def run_tfim(binding, torch, W, cases=((14, 100, 10), (16, 100, 3)), dt=0.2):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the halved
-# two-pass launch, from one ncu capture of a 16384-shift slice at N = 20 in
-# the tuning below (37.361 GB read + 58.768 GB written), scaled by shifts to
-# the 2^20 - 4096 halved shifts of one evaluation.  Valid only for that
-# kernel build and tuning; any other run reports null.
-TRAFFIC_SLICE_BYTES = 37.360901e9 + 58.768246e9
+# launch, from one ncu capture of a 16384-shift slice at N = 20 per mode and
+# tuning, scaled by shifts to the 2^20 - 4096 halved shifts of one
+# evaluation.  Valid only for that kernel build and tuning; any other run
+# reports null.
+TRAFFIC = {
+    # FP32 CUDA-core two-pass kernel (37.361 GB read + 58.768 GB written)
+    ("fp32", (2, 11, 5, 3, 1)): 37.360901e9 + 58.768246e9,
+    # tensor-core kernel, FP16 pieces (71.515 GB read + 68.572 GB written)
+    ("fp16_split", (2, 11, 5, 5, 1)): 71.514731e9 + 68.571581e9,
+}
 TRAFFIC_SLICE_SHIFTS = 16384
-TRAFFIC_TUNING = {"x_batch_log": 2, "ring_slots": 11, "lag": 5, "pass2_tiles_log": 3,
-                  "pass1_blocks_log": 1, "pass1_staged": 1, "pass2_staged": 1}
 TRAFFIC_SOURCE = ("ncu --set full, 16384 halved shifts at N=20, scaled by shifts "
                   "to the halved launch (the x < 4096 launch adds < 1 %)")
 
 
 def profiled_traffic(N, mode, tuning):
-    if N != 20 or mode != "fp32" or tuning != TRAFFIC_TUNING:
+    if N != 20 or not tuning:
         return None
-    return TRAFFIC_SLICE_BYTES * ((1 << N) - 4096) / TRAFFIC_SLICE_SHIFTS
+    key = (mode, (tuning["x_batch_log"], tuning["ring_slots"], tuning["lag"], tuning["pass2_tiles_log"],
+                  tuning["pass1_blocks_log"]))
+    b = TRAFFIC.get(key)
+    if b is None:
+        return None
+    return b * ((1 << N) - 4096) / TRAFFIC_SLICE_SHIFTS
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -644,7 +656,8 @@ def run_gpu(args):
         peak_t = peaks.get("bf16_tflops_sustained", 1700.0)
         roof = {
             "bound": "tensor", "kernel": kname, "achieved": tflops, "peak": peak_t, "unit": "TFLOP/s",
-            "frac": tflops / peak_t, "traffic": None, "traffic_source": "not captured for this mode",
+            "frac": tflops / peak_t, "traffic": profiled_traffic(N, args.mode, tuning),
+            "traffic_source": TRAFFIC_SOURCE,
             "peak_source": f"MEASURED_PEAKS bf16_tflops_sustained ({peak_src}); fp16 runs at the bf16 rate",
             "mma_flops_per_launch": tc_mma_flops(N), "kernel_ms": statistics.mean(kern_ms),
             "alu_frac_algorithmic": achieved / peak_ops if peak_ops else None,
@@ -692,7 +705,8 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.mode != "fp64" else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16_split": "f16x2-split (f32 accumulate)",
+                  "bf16_split": "bf16x2-split (f32 accumulate)"}.get(args.mode, args.mode),
         "data": "synthetic",
         "config": {"workload": f"N={N} Haar-random state (complex64), all 4^{N} Pauli strings per step",
                    "N": N, "states_per_gpu": 1, "mode": args.mode, "l2_flush": "512 MiB write between steps",

@@ -278,10 +278,29 @@ SRE_API sre_status_t sre_sum_pow_range(sre_plan_t plan, const void *d_state, int
                                        double *d_out, double *d_per_x);
 
 /*
+ * The last step of Algorithm 1 for sums reduced elsewhere (for example the
+ * all-reduce of sre_sum4_range / sre_sum_pow_range partials over shards of
+ * the shifts): Eq. (final1) at order 2 and Eq. (sre) at integer order alpha,
+ *     *d_m = log2(S / (d n2^(2 alpha))) / (1 - alpha),   d = 2^N,
+ * so M2 = -log2(S / (d n2^4)).  d_S and d_n2: device doubles holding the
+ * total sum S_alpha and n2 = <psi|psi>; d_m: device double receiving the
+ * result (NaN unless S and n2 are finite and > 0).  All three are owned by
+ * the caller and must be 8-byte aligned (SRE_EALIGN).  SRE_EINVAL for a
+ * null pointer, N outside [1, SRE_MAX_QUBITS] or alpha outside
+ * [2, SRE_MAX_ORDER].  Asynchronous on `stream`; needs no plan.
+ */
+SRE_API sre_status_t sre_m_alpha_from_sums(const double *d_S, const double *d_n2, int N, int alpha,
+                                           sre_stream_t stream, double *d_m);
+
+/*
  * M2 of `count` states of uneven size in one submission (states may have
- * different N, each <= the plan's N).  d_states: host array of `count`
+ * different N, each <= the plan's N): Algorithm 1 with Eq. (final1) per
+ * state, the paper's loop over states of one experiment (the realizations
+ * and time steps of its Examples 1 and 2) folded into one launch sequence.
+ * d_states: host array of `count`
  * device pointers; Ns: host array of the N_i; d_m2_out: device array of
- * `count` doubles (NaN for a zero / non-finite state).  The batch is
+ * `count` doubles (NaN for a zero / non-finite state, and for every state
+ * of a submission in which a device wait expired).  The batch is
  * executed by persistent kernels walking one work list, and is replayed
  * from a captured CUDA graph when the same (pointers, Ns) batch is
  * submitted again.  Asynchronous.  Errors: SRE_EINVAL, SRE_EALIGN,
@@ -299,7 +318,10 @@ SRE_API sre_status_t sre_m2_batched(sre_plan_t plan, const void *const *d_states
  *   d_state: device buffer of 2^N interleaved (re, im) float pairs, 8-byte
  *            aligned, 1 <= N <= SRE_NOALLOC_MAX_QUBITS (16); larger N is
  *            rejected with SRE_EINVAL before anything is launched.
- *   d_m2:    device double receiving M2 (NaN for a zero / non-finite state).
+ *   d_m2:    device double receiving M2; NaN for a zero / non-finite state,
+ *            and NaN as well when a device wait of the two-pass kernel
+ *            expires (fixed limit of 5 s): the status the kernel records
+ *            stays in the library's own array, out of the caller's reach.
  * Asynchronous on `stream`.  Its only scratch is one fixed module array of
  * about 5.4 MB that every GPU loading the library holds until exit; the
  * first call with a device current looks up that array's address and must
@@ -321,6 +343,9 @@ SRE_API sre_status_t sre_selftest_wait_timeout(uint64_t wait_ns, sre_stream_t st
 
 /* ----------------------------------------------------------------------- */
 /* Serving: continuous batching of M2 requests of mixed N.                  */
+/* The paper has no serving layer; each request is Algorithm 1 with         */
+/* Eq. (final1), evaluated by the single-state path (N > 16) or merged with */
+/* other small requests into one sre_m2_batched-style submission.           */
 /* ----------------------------------------------------------------------- */
 
 typedef struct sre_server_s *sre_server_t;
@@ -343,7 +368,7 @@ typedef struct {
     uint64_t resident_bytes, peak_resident_bytes;
 } sre_server_stats_t;
 
-/* Fill cfg with defaults (HBM budget 8 GiB, 32 slots, 4096 queued,
+/* Fill cfg with defaults (HBM budget 8 GiB, 4 slots, 4096 queued,
  * max_N 20, FP32, 5 s wait limit, device 0). */
 SRE_API void sre_server_cfg_default(sre_server_cfg_t *cfg);
 
@@ -356,8 +381,10 @@ SRE_API sre_status_t sre_server_create(const sre_server_cfg_t *cfg, sre_server_t
  * them, in host memory if on_device == 0 or device memory if 1.  The
  * server copies the state into memory it owns before returning, so the
  * caller may reuse its buffer at once.  *ticket identifies the request.
- * Errors: SRE_EINVAL, SRE_EBUSY (queue full, or the request alone exceeds
- * the HBM budget), SRE_ENOMEM.
+ * on_device must say where `state` lives (it selects the copy's
+ * direction; the pointer is not inspected).  Errors: SRE_EINVAL, SRE_EBUSY
+ * (queue full, or the request does not fit the HBM budget next to what is
+ * resident), SRE_ENOMEM, SRE_ECUDA (the copy failed).
  */
 SRE_API sre_status_t sre_server_submit(sre_server_t srv, const void *state, int on_device, int N,
                                sre_dtype_t dtype, uint64_t *ticket);
@@ -365,11 +392,14 @@ SRE_API sre_status_t sre_server_submit(sre_server_t srv, const void *state, int 
 /* Non-blocking poll: *done = 1 and *m2 set once the request finished
  * (M2 is NaN for a zero / non-finite state); *done = 0 otherwise.  A
  * finished ticket is forgotten after it has been polled done once.
- * SRE_ENOTFOUND for an unknown ticket, SRE_ETIMEDOUT if its device wait
- * expired. */
+ * SRE_ENOTFOUND for an unknown ticket; SRE_ETIMEDOUT (with *done = 1 and
+ * M2 NaN) if a device wait of the launch that evaluated it expired -- for
+ * a request merged with others, a wait anywhere in that launch; SRE_ECUDA
+ * if that launch failed. */
 SRE_API sre_status_t sre_server_poll(sre_server_t srv, uint64_t ticket, int *done, double *m2);
 
-/* Block until `ticket` is done or timeout_ms elapses (SRE_ETIMEDOUT). */
+/* Block until `ticket` is done or timeout_ms elapses (SRE_ETIMEDOUT, the
+ * ticket stays valid); a finished request returns as sre_server_poll. */
 SRE_API sre_status_t sre_server_wait(sre_server_t srv, uint64_t ticket, double timeout_ms, double *m2);
 
 SRE_API sre_status_t sre_server_stats(sre_server_t srv, sre_server_stats_t *stats);

@@ -109,6 +109,7 @@ def _declare(lib):
         "sre_sum_pow_range": (S, [_vp, _vp, _i, _i, _u64, _u64, _vp, _vp, _vp]),
         "sre_m2_batched": (S, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), _i, _vp, _vp]),
         "sre_selftest_wait_timeout": (S, [_u64, _vp]),
+        "sre_m_alpha_from_sums": (S, [_vp, _vp, _i, _i, _vp, _vp]),
         "sre_server_cfg_default": (None, [ctypes.POINTER(ServerCfg)]),
         "sre_server_create": (S, [ctypes.POINTER(ServerCfg), ctypes.POINTER(_vp)]),
         "sre_server_submit": (S, [_vp, _vp, _i, _i, _i, ctypes.POINTER(_u64)]),
@@ -391,6 +392,22 @@ class Plan:
         _check(load_library().sre_m2_batched(self._h, ptrs, Ns, n, _stream_handle(stream),
                                              ctypes.c_void_p(out.data_ptr())), "sre_m2_batched")
         return out
+
+
+def m_alpha_from_sums(S, n2, N: int, alpha: int = 2, stream=None):
+    """sre_m_alpha_from_sums: M_alpha (M2 at alpha = 2) from device scalars
+    S_alpha and n2 (CUDA float64 tensors of one element); returns a CUDA
+    float64 tensor of one element, computed on `stream` (default: torch's
+    current stream)."""
+    torch = _torch()
+    for t in (S, n2):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.numel() == 1):
+            raise ValueError("S and n2 must be one-element CUDA float64 tensors")
+    out = torch.empty(1, dtype=torch.float64, device=S.device)
+    _check(load_library().sre_m_alpha_from_sums(
+        ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(n2.data_ptr()), int(N), int(alpha),
+        _stream_handle(stream), ctypes.c_void_p(out.data_ptr())), "sre_m_alpha_from_sums")
+    return out
 
 
 def selftest_wait_timeout(wait_ns: int = 200_000_000, stream=None) -> int:

@@ -590,6 +590,15 @@ sre_status_t sre_selftest_wait_timeout(uint64_t wait_ns, sre_stream_t stream) {
     return st == -1 ? SRE_OK : (sre_status_t)st;
 }
 
+sre_status_t sre_m_alpha_from_sums(const double *d_S, const double *d_n2, int N, int alpha,
+                                   sre_stream_t stream, double *d_m) {
+    if (!d_S || !d_n2 || !d_m || N < 1 || N > SRE_MAX_QUBITS || alpha < 2 || alpha > SRE_MAX_ORDER)
+        return SRE_EINVAL;
+    if (((uintptr_t)d_S) % 8 || ((uintptr_t)d_n2) % 8 || ((uintptr_t)d_m) % 8) return SRE_EALIGN;
+    cudaError_t e = sre::enqueue_malpha_from_sums(d_S, d_n2, N, alpha, d_m, (cudaStream_t)stream);
+    return e == cudaSuccess ? SRE_OK : cuda_fail(e);
+}
+
 sre_status_t sre_m2_batched(sre_plan_t p, const void *const *d_states, const int *Ns, int count,
                             sre_stream_t stream, double *d_m2_out) {
     if (!p || !d_states || !Ns || !d_m2_out || count < 1 || count > 65535) return SRE_EINVAL;

@@ -43,6 +43,7 @@ struct GraphEntry {
     std::vector<int> Ns;
     sre_mode_t mode;
     double *out;
+    int *status_out = nullptr;
     // per-entry device tables (stable for replays)
     const void **d_ptrs = nullptr;
     int *d_Ns = nullptr;
@@ -127,18 +128,19 @@ static cudaError_t enqueue_entry(BatchedContext *ctx, const Workspace &ws, const
         first += (size_t)L.S;
     }
     return enqueue_batch_finalize(ws, g.d_seg, ctx->parts, ctx->npart, ctx->flags, g.d_Ns, g.d_out,
-                                  count, g.out, st);
+                                  count, g.out, g.status_out, st);
 }
 
 cudaError_t batched_run(BatchedContext *ctx, const Workspace &ws, const DeviceInfo &dev,
                         const void *const *d_states, const int *Ns, int count, sre_dtype_t dtype,
                         sre_mode_t mode, cudaStream_t stream, double *d_m2_out, long long wait_ns,
-                        const LargeCfg *const *tuned_half, bool capture) {
+                        const LargeCfg *const *tuned_half, bool capture, int *d_status_out) {
     cudaError_t e;
     // ---- replay an existing graph for an identical batch
     for (size_t k = 0; k < ctx->graphs.size(); ++k) {
         GraphEntry &g = ctx->graphs[k];
-        if (g.mode != mode || g.out != d_m2_out || (int)g.ptrs.size() != count) continue;
+        if (g.mode != mode || g.out != d_m2_out || g.status_out != d_status_out || (int)g.ptrs.size() != count)
+            continue;
         if (!std::equal(g.ptrs.begin(), g.ptrs.end(), d_states) || !std::equal(g.Ns.begin(), g.Ns.end(), Ns))
             continue;
         if (g.exec && g.generation == ctx->generation) {
@@ -207,6 +209,7 @@ cudaError_t batched_run(BatchedContext *ctx, const Workspace &ws, const DeviceIn
     g.Ns.assign(Ns, Ns + count);
     g.mode = mode;
     g.out = d_m2_out;
+    g.status_out = d_status_out;
     g.generation = ctx->generation;
     const bool fp64 = mode == SRE_MODE_FP64;
     const bool convert = (int)dtype != (fp64 ? SRE_C128 : SRE_C64);

@@ -140,8 +140,11 @@ cudaError_t enqueue_batch_norm(const Workspace &ws, const void *const *d_ptrs, c
 cudaError_t enqueue_batch_finalize(const Workspace &ws, const void *seg, const double *parts,
                                    const double *npart, const int *flags, const int *d_Ns,
                                    const int *d_out_index, int count, double *m2_out,
-                                   cudaStream_t st);
+                                   int *status_out, cudaStream_t st);
 cudaError_t enqueue_convert(const void *src, sre_dtype_t from, void *dst, int N, cudaStream_t st);
+// out = M_alpha from device scalars S and n2 (NaN unless both are finite and > 0).
+cudaError_t enqueue_malpha_from_sums(const double *S, const double *n2, int N, int alpha, double *out,
+                                     cudaStream_t st);
 
 // Single-pass kernel (sre_mid.cu) for shift ranges whose transform spans one,
 // two or (FP32, elem_bytes 8) four 4096-entry blocks: one FP64 partial per

@@ -180,6 +180,13 @@ __global__ void k_finalize(const double *__restrict__ parts, long long o1, long 
     }
 }
 
+// M_alpha from a reduced sum and a norm (sums of shards added elsewhere).
+__global__ void k_malpha_from_sums(const double *S, const double *n2, int N, int alpha, double *out) {
+    const double s = *S, n = *n2;
+    const bool bad = !(s > 0.0) || !(n > 0.0) || !isfinite(s) || !isfinite(n);
+    *out = malpha_from(s, n, N, alpha, bad);
+}
+
 __global__ void k_copy_sums(const Result *res, double *out2) {
     out2[0] = res->S;
     out2[1] = res->n2;
@@ -587,8 +594,10 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
 
 // M2 of one complex64 state in FP32 with fixed two-pass configurations for
 // both shift ranges (no allocation, no autotuning): used by callers that
-// hand in preassigned scratch.  Same kernels and launch sequence as the
-// FP32 single-state path.
+// hand in preassigned scratch.  It shares the norm and finalize kernels
+// with the single-state path, but runs the two-pass kernel with the given
+// fixed configuration for every N > 12: no single-pass kernel for
+// N = 13..15 and no autotuned plan.
 cudaError_t enqueue_m2_fixed(const Workspace &ws, const DeviceInfo &dev, const void *psi, int N,
                              const LargeCfg &cfg_full, const LargeCfg &cfg_half, cudaStream_t st,
                              double *d_m2, long long wait_ns) {
@@ -719,19 +728,25 @@ __global__ void __launch_bounds__(kThreads) k_norm_batch(const void *const *__re
 
 // M2 of every state of a batch: one warp per state, the same fixed-order
 // segment sums as the single-state finalize (seg = {off1, n1, off2, n2}).
+// status_out (may be null) receives each state's status with the same
+// precedence as k_finalize: the batch's device-wait status first, then a
+// non-finite amplitude, then a zero norm.
 __global__ void k_finalize_batch(const longlong4 *__restrict__ seg, const double *__restrict__ parts,
                                  const double *__restrict__ npart, int nnorm,
                                  const int *__restrict__ flags, const int *__restrict__ Ns,
                                  const int *__restrict__ out_index, int count, const int *status,
-                                 double *__restrict__ m2_out) {
+                                 double *__restrict__ m2_out, int *__restrict__ status_out) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= count) return;
     const longlong4 g = seg[w];
     const double S = warp_sum_segments(parts, g.x, g.y, g.z, g.w);
     const double n = warp_sum_segments(npart, (long long)w * nnorm, nnorm, 0, 0);
     if ((threadIdx.x & 31) == 0) {
-        const bool bad = (*status != 0) || (flags[w] & kFlagNonFinite) || !(n > 0.0);
-        m2_out[out_index[w]] = m2_from(S, n, Ns[w], bad);
+        int st = *status;
+        if (st == 0 && (flags[w] & kFlagNonFinite)) st = SRE_ENONFINITE;
+        if (st == 0 && !(n > 0.0)) st = SRE_EZERO;
+        m2_out[out_index[w]] = m2_from(S, n, Ns[w], st != 0);
+        if (status_out) status_out[out_index[w]] = st;
     }
 }
 
@@ -871,13 +886,19 @@ cudaError_t enqueue_batch_norm(const Workspace &ws, const void *const *d_ptrs, c
 cudaError_t enqueue_batch_finalize(const Workspace &ws, const void *seg, const double *parts,
                                    const double *npart, const int *flags, const int *d_Ns,
                                    const int *d_out_index, int count, double *m2_out,
-                                   cudaStream_t st) {
+                                   int *status_out, cudaStream_t st) {
     const int threads = 256;
     const int blocks = (count * 32 + threads - 1) / threads;
     k_finalize_batch<<<blocks, threads, 0, st>>>(reinterpret_cast<const longlong4 *>(seg), parts, npart,
                                                  kNormBlocks, flags, d_Ns, d_out_index, count,
-                                                 ws.status, m2_out);
+                                                 ws.status, m2_out, status_out);
     ws.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_malpha_from_sums(const double *S, const double *n2, int N, int alpha, double *out,
+                                     cudaStream_t st) {
+    k_malpha_from_sums<<<1, 1, 0, st>>>(S, n2, N, alpha, out);
     return cudaGetLastError();
 }
 

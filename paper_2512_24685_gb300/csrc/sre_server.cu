@@ -12,7 +12,9 @@
 // batched evaluation; a large request gets a slot of its own.  Completion is
 // detected with CUDA events; latencies (submit -> result on the host) feed
 // p50/p99.  Device-side waits inside the kernels are bounded by the
-// configured wait limit.
+// configured wait limit; every request carries the status its evaluation
+// recorded on the device (a merged batch whose wait expired marks all of
+// its requests SRE_ETIMEDOUT).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +58,8 @@ struct Slot {
     cudaEvent_t ev = nullptr;
     double *d_out = nullptr;   // kBatchMaxCount
     double *h_out = nullptr;   // pinned
+    int *d_st = nullptr;       // kBatchMaxCount per-request statuses
+    int *h_st = nullptr;       // pinned
     sre::Result *h_res = nullptr;  // pinned (single-request path)
     std::vector<uint64_t> tickets;  // in flight
     bool single = false;
@@ -161,10 +165,12 @@ void launch_unit(sre_server_s *s, Slot &sl) {
         }
         e = sre::batched_run(sl.batched, sl.ws, s->dev, ptrs.data(), Ns.data(), (int)take.size(), dt,
                              s->cfg.mode, sl.stream, sl.d_out, (long long)s->cfg.wait_limit_ns, nullptr,
-                             /*capture=*/false);
+                             /*capture=*/false, sl.d_st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(sl.h_out, sl.d_out, sizeof(double) * take.size(), cudaMemcpyDeviceToHost,
                                 sl.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sl.h_st, sl.d_st, sizeof(int) * take.size(), cudaMemcpyDeviceToHost, sl.stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
     if (e != cudaSuccess) {
@@ -188,8 +194,7 @@ void collect(sre_server_s *s, Slot &sl) {
         } else if (sl.single) {
             finish(s, r, sl.h_res->m2, sl.h_res->status);
         } else {
-            const double m = sl.h_out[i];
-            finish(s, r, m, std::isnan(m) ? SRE_ENONFINITE : 0);
+            finish(s, r, sl.h_out[i], sl.h_st[i]);
         }
     }
     sl.tickets.clear();
@@ -231,6 +236,8 @@ void destroy_slots(sre_server_s *s) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
         cudaFree(sl.d_out);
         cudaFreeHost(sl.h_out);
+        cudaFree(sl.d_st);
+        cudaFreeHost(sl.h_st);
         cudaFreeHost(sl.h_res);
     }
     s->slots.clear();
@@ -280,6 +287,8 @@ sre_status_t sre_server_create(const sre_server_cfg_t *cfg, sre_server_t *out) {
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_out, sizeof(double) * kBatchMaxCount);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, sizeof(double) * kBatchMaxCount);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_st, sizeof(int) * kBatchMaxCount);
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_st, sizeof(int) * kBatchMaxCount);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_res, sizeof(sre::Result));
         sl.batched = sre::batched_create(s->dev);
         if (e != cudaSuccess || !sl.batched) {

@@ -6,7 +6,9 @@
 * admission by HBM bytes rejects what does not fit (SRE_EBUSY);
 * a bad state comes back as NaN, an unknown ticket as SRE_ENOTFOUND;
 * a device wait that nothing satisfies ends with SRE_ETIMEDOUT and leaves
-  the context usable.
+  the context usable;
+* a merged batch whose device wait expired reports SRE_ETIMEDOUT for its
+  requests.
 """
 import time
 
@@ -117,3 +119,39 @@ def test_server_admission_by_hbm_bytes(sre, torch_cuda):
         st = srv.stats()
         assert st["rejected"] == 1 and st["completed"] == 1
         assert st["peak_resident_bytes"] <= slot_bytes + (300 << 10)
+
+
+def _poll_status(sre, srv, ticket, timeout_s=60.0):
+    """(status, m2) of a finished ticket through sre_server_poll."""
+    end = time.perf_counter() + timeout_s
+    while time.perf_counter() < end:
+        try:
+            done, m = srv.poll(ticket)
+        except sre.SreError as e:
+            return e.status, float("nan")
+        if done:
+            return 0, m
+        time.sleep(0.001)
+    raise AssertionError("request did not finish")
+
+
+def test_server_merged_batch_reports_device_timeout(sre, torch_cuda):
+    """A merged batch of N = 16 requests (two-pass kernel, bounded device
+    waits) under a 1 ns wait limit: a request whose batch had a wait expire
+    comes back from poll as SRE_ETIMEDOUT, not as SRE_OK with a NaN, and one
+    whose batch finished has the correct M2."""
+    states = [W.haar_state(16, 900 + k, np.complex64) for k in range(8)]
+    with sre.Server(max_inflight=1, max_N=16, hbm_budget_bytes=4 << 30, wait_limit_ns=1) as srv:
+        tickets = [srv.submit(v) for v in states]
+        res = [_poll_status(sre, srv, t) for t in tickets]
+        st = srv.stats()
+    statuses = [s for s, _ in res]
+    assert set(statuses) <= {0, 7}, statuses
+    assert 7 in statuses, statuses
+    assert st["failed"] == statuses.count(7)
+    for (s, m), v in zip(res, states):
+        if s == 0:
+            assert abs(m - oracle.m2(v)) <= 1e-6
+    # the server stays usable with an ordinary limit afterwards
+    with sre.Server(max_inflight=1, max_N=16) as srv:
+        assert abs(srv.wait(srv.submit(states[0]), 60000) - oracle.m2(states[0])) <= 1e-6

@@ -39,11 +39,15 @@ def test_brickwork_gate_tensor_reproduces_brickwork_state():
 
 
 def test_bench_traffic_only_for_profiled_configuration():
+    """roofline.traffic is reported only for a (mode, tuning) pair that an
+    ncu capture measured, scaled from the slice to the halved launch."""
     import bench
-    tun = dict(bench.TRAFFIC_TUNING)
-    full = bench.profiled_traffic(20, "fp32", tun)
-    assert full == bench.TRAFFIC_SLICE_BYTES * ((1 << 20) - 4096) / bench.TRAFFIC_SLICE_SHIFTS
-    assert bench.profiled_traffic(19, "fp32", tun) is None
-    assert bench.profiled_traffic(20, "fp64", tun) is None
-    tun["ring_slots"] += 1
-    assert bench.profiled_traffic(20, "fp32", tun) is None
+    keys = ("x_batch_log", "ring_slots", "lag", "pass2_tiles_log", "pass1_blocks_log")
+    for (mode, tup), slice_bytes in bench.TRAFFIC.items():
+        tun = dict(zip(keys, tup))
+        full = bench.profiled_traffic(20, mode, tun)
+        assert full == slice_bytes * ((1 << 20) - 4096) / bench.TRAFFIC_SLICE_SHIFTS
+        assert bench.profiled_traffic(19, mode, tun) is None
+        assert bench.profiled_traffic(20, "fp64", tun) is None
+        tun["ring_slots"] += 1
+        assert bench.profiled_traffic(20, mode, tun) is None

@@ -47,7 +47,8 @@ def _worker(rank, world, port, N, seed, fail_rank, q):
 
         def partial(b, e):
             return oracle.sum4_xorfwht(psi, b, e), oracle.norm2(psi)
-        m2 = shard.m2_sharded(psi, N, partial_fn=partial)
+        S, n2 = shard.sum_sharded(N, partial)
+        m2 = oracle.m2_from_sum(S, n2, N)
         q.put((rank, "ok", m2))
     except Exception as exc:  # reported to the parent
         q.put((rank, "error", repr(exc)))

@@ -3,9 +3,12 @@
 This entry point exists for callers that cannot allocate memory where they
 need M2 (for example inside a region where cudaMalloc is unsafe, or under a
 fixed memory budget).  The test calls it through the C ABI and checks its
-result against the ordinary entry point (sre_m2, via a plan) with the FP32
-tolerance the other tests use, on two calls in a row per size, so a second
-call that reuses the shared array (and its leftover contents) is covered.
+result against the ordinary entry point (sre_m2, via a plan) and against the
+FP64 oracle (Algorithm 1) with the FP32 tolerance the other tests use, on two
+calls in a row per size, so a second call that reuses the shared array (and
+its leftover contents) is covered.  The sizes span the single-tile path
+(N = 1, 2, 3, 12), the two-pass kernel on the fixed ring (13 to 16, with
+N = 15 the last halved size below the limit).
 It is collected last and sets up everything it needs itself, so it passes in
 a fresh process as well as after the rest of the suite.
 """
@@ -13,6 +16,8 @@ import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -41,16 +46,20 @@ def _noalloc(torch, f, psi_dev, N):
     return out.item()
 
 
-@pytest.mark.parametrize("N", [3, 12, 13, 14, 16])
+@pytest.mark.parametrize("N", [1, 2, 3, 12, 13, 14, 15, 16])
 def test_noalloc_matches_plan_twice(env, N):
     torch, binding, W, f = env
-    psi = torch.from_numpy(W.haar_state(N, 77 + N, np.complex64)).cuda()
+    host = W.haar_state(N, 77 + N, np.complex64)
+    psi = torch.from_numpy(host).cuda()
     with binding.Plan(N, "c64") as p:
         ref = p.m2(psi)
+    want = oracle.m2(host)
     first = _noalloc(torch, f, psi, N)
     second = _noalloc(torch, f, psi, N)
     assert abs(first - ref) <= TOL, (first, ref)
     assert abs(second - ref) <= TOL, (second, ref)
+    assert abs(first - want) <= TOL, (first, want)
+    assert abs(second - want) <= TOL, (second, want)
     # a different state in between must not leak through the shared array
     other = torch.from_numpy(W.haar_state(N, 999, np.complex64)).cuda()
     _noalloc(torch, f, other, N)

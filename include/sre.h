@@ -73,12 +73,20 @@ typedef enum {
 
 /* Arithmetic used for the product, the transform and the per-element
  * |A|^4; the cross-shift accumulation, the norm and the final log are FP64
- * in every mode. */
+ * in every mode.  The split modes apply to complex64 states and take the
+ * halved shifts (x >= 4096) of 16-byte aligned states with 16 <= N <= 20
+ * (other sizes run wholly in FP32) through two
+ * tensor-core Hadamard stages of 128 x 128: each operand is scaled by a
+ * power of two and split into an integer high piece (|hi| <= 2^8 for bf16,
+ * 2^11 for fp16) and the remainder rounded to the 16-bit type as the low
+ * piece.  The Hadamard matrix is +-1, so the high piece's sums are exact in
+ * the FP32 accumulator and the low piece adds the next 8 (bf16) or 11
+ * (fp16) significant bits; the remaining shifts run in FP32.  Value 3 is unused (a tf32 split would need the same two
+ * pieces at half the bf16 tensor rate and twice the operand bytes). */
 typedef enum {
     SRE_MODE_FP32 = 0,       /* CUDA-core FP32 butterflies */
-    SRE_MODE_BF16_SPLIT = 1, /* tensor-core Hadamard stages, bf16 hi/lo split, FP32 accumulate */
-    SRE_MODE_FP16_SPLIT = 2, /* tensor-core Hadamard stages, fp16 hi/lo split, FP32 accumulate */
-    SRE_MODE_TF32_SPLIT = 3, /* tensor-core Hadamard stages, tf32 hi/lo split, FP32 accumulate */
+    SRE_MODE_BF16_SPLIT = 1, /* tensor-core Hadamard stages, bf16 hi/lo fixed-point split */
+    SRE_MODE_FP16_SPLIT = 2, /* tensor-core Hadamard stages, fp16 hi/lo fixed-point split */
     SRE_MODE_FP64 = 4,       /* CUDA-core FP64 everywhere */
     SRE_MODE_AUTO = -1       /* the plan's tuned default */
 } sre_mode_t;

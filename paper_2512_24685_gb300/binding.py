@@ -29,7 +29,7 @@ _lib = None
 
 MAX_QUBITS = 24
 DTYPES = {"c64": 0, "c128": 1}
-MODES = {"fp32": 0, "bf16_split": 1, "fp16_split": 2, "tf32_split": 3, "fp64": 4, "auto": -1}
+MODES = {"fp32": 0, "bf16_split": 1, "fp16_split": 2, "fp64": 4, "auto": -1}
 STATUS = {
     0: "SRE_OK", 1: "SRE_EINVAL", 2: "SRE_EALIGN", 3: "SRE_EZERO", 4: "SRE_ENONFINITE",
     5: "SRE_ENOMEM", 6: "SRE_EBUSY", 7: "SRE_ETIMEDOUT", 8: "SRE_ECUDA", 9: "SRE_ENOTFOUND",

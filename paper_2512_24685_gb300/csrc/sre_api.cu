@@ -148,7 +148,7 @@ sre_status_t sre_plan_create(int N, sre_dtype_t dtype, sre_plan_t *out) {
 sre_status_t sre_plan_set_mode(sre_plan_t p, sre_mode_t mode) {
     if (!p) return SRE_EINVAL;
     if (mode == SRE_MODE_AUTO) mode = p->dtype == SRE_C128 ? SRE_MODE_FP64 : SRE_MODE_FP32;
-    if ((int)mode < 0 || (int)mode > (int)SRE_MODE_FP64) return SRE_EINVAL;
+    if ((int)mode < 0 || (int)mode > (int)SRE_MODE_FP64 || (int)mode == 3) return SRE_EINVAL;
     if (!mode_supported(mode)) return SRE_EUNSUPPORTED;
     if (elem_bytes_for_mode(mode) != elem_bytes_for_mode(p->mode) || !p->ws.result) {
         cudaError_t e = cudaDeviceSynchronize();

@@ -23,7 +23,7 @@ cudaError_t batched_run(BatchedContext *ctx, const Workspace &ws, const DeviceIn
                         const LargeCfg *const *tuned_half, bool capture = true,
                         int *d_status_out = nullptr);
 
-// Tensor-core split-precision modes (BF16 / FP16 / TF32 hi-lo Hadamard stages).
+// Tensor-core split-precision modes (BF16 / FP16 hi-lo fixed-point Hadamard stages).
 bool tc_mode_available(sre_mode_t mode);
 cudaError_t tc_enqueue_m2(const Workspace &ws, const DeviceInfo &dev, const void *d_state,
                           sre_dtype_t dtype, int N, uint64_t x_begin, uint64_t x_end,

@@ -631,8 +631,11 @@ def run_gpu(args):
     clocks = sampler.summary() if sampler else {}
     max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     # FP32 ALU roofline: SMs x 128 FP32 lanes x max SM clock (one add / mul /
-    # fma per lane per clock); algorithmic ops per state (2N + 11) 4^N.
-    alg_ops = (2 * N + 11) * terms
+    # fma per lane per clock); algorithmic ops (2N + 11) d per Pauli term,
+    # over the terms of the timed launch (the halved shifts x >= 4096; the
+    # plan's profiling events bracket that launch alone)
+    timed_terms = float(d) * (d - 4096) if N > 12 else terms
+    alg_ops = (2 * N + 11) * timed_terms
     kern_s = statistics.mean(kern_ms) / 1000.0
     if args.mode == "fp64":
         peak_ops = None

@@ -162,10 +162,12 @@ SRE_API sre_status_t sre_plan_autotune(sre_plan_t plan, int N, sre_stream_t stre
                                        sre_tuning_t *best, double *ms);
 
 /* Profiling support.  When enabled (enable != 0), the plan records two CUDA
- * events on the stream around the main transform kernel of each evaluation;
- * sre_plan_last_kernel_ms waits for the second event and returns the
- * elapsed milliseconds of the last evaluation's main kernel and its name
- * (static string).  sre_plan_launch_count returns the number of kernels
+ * events on the stream around the main transform launch of each
+ * evaluation: for N > 12 the launch of the conjugate-symmetry halved
+ * shifts x >= 4096 (k_large, k_mid or k_tc; 99.6 % of the shifts at
+ * N = 20), else the single-tile kernel.  sre_plan_last_kernel_ms waits for
+ * the second event and returns the elapsed milliseconds of the last
+ * evaluation's main launch and its kernel's name (static string).  sre_plan_launch_count returns the number of kernels
  * the plan has launched since it was created (its own kernels only). */
 SRE_API sre_status_t sre_plan_set_profiling(sre_plan_t plan, int enable);
 SRE_API sre_status_t sre_plan_last_kernel_ms(sre_plan_t plan, double *ms, const char **name);

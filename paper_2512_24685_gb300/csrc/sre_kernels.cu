@@ -546,12 +546,16 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
             return e;
         if ((e = cudaMemsetAsync(ws.work, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess) return e;
         size_t chunks = 0;
-        if (ws.ev_begin && (e = cudaEventRecord(ws.ev_begin, st)) != cudaSuccess) return e;
         for (int half = 0; half <= 1; ++half) {
             const uint64_t xb = half ? split : x_begin;
             const uint64_t xe = half ? x_end : split;
             if (xb >= xe) continue;
             const bool tc_here = tc_kind && tc_applies(N, half, alpha, psi);
+            // the profiling events bracket the dominant launch: the halved
+            // shifts, or the full-transform range when there are none
+            const bool timed = half == 1 || split >= x_end;
+            if (timed && !tc_here && ws.ev_begin && (e = cudaEventRecord(ws.ev_begin, st)) != cudaSuccess)
+                return e;
             if (!tc_here && mid_applies(N, half, eb)) {
                 // one or two blocks per shift: single pass, one partial per shift
                 const long long ns = (long long)(xe - xb);
@@ -559,6 +563,8 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
                 if ((e = launch_mid<R>(N, half, psi, nullptr, 1, ns, xb, alpha, ws.chunk_sum + chunks,
                                        d_per_x ? d_per_x + (xb - x_begin) : nullptr, dev, st)) != cudaSuccess)
                     return e;
+                if (timed && ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
+                if (timed) ws.main_kernel = "k_mid";
                 ws.launches += 1;
                 chunks += (size_t)ns;
                 if (!half) seg1 = (long long)chunks;
@@ -578,12 +584,14 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
             else
                 e = launch_large<R, false>(a, grid, st);
             if (e != cudaSuccess) return e;
+            if (timed && !tc_here) {
+                if (ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
+                ws.main_kernel = "k_large";
+            }
             ws.launches += 1;
             chunks += (size_t)a.n_chunks;
             if (!half) seg1 = (long long)chunks;
         }
-        if (ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
-        ws.main_kernel = "k_large";
         parts = ws.chunk_sum;
         nparts = (long long)chunks;
     }

@@ -872,9 +872,14 @@ cudaError_t launch_large_tc(const LargeArgs &a, const Workspace &ws, const Devic
     LargeArgs b = a;
     b.tc_e = ws.tc_e;
     grid = std::max(1, std::min(grid, dev.sms));  // one CTA per SM (all of TMEM)
-    if (tc_kind == kTcBf16) return launch_tc<kTcBf16>(b, grid, st);
-    if (tc_kind == kTcFp16) return launch_tc<kTcFp16>(b, grid, st);
-    return cudaErrorInvalidValue;
+    if (tc_kind != kTcBf16 && tc_kind != kTcFp16) return cudaErrorInvalidValue;
+    // the profiling events bracket the tensor-core kernel alone
+    if (ws.ev_begin && (e = cudaEventRecord(ws.ev_begin, st)) != cudaSuccess) return e;
+    e = tc_kind == kTcBf16 ? launch_tc<kTcBf16>(b, grid, st) : launch_tc<kTcFp16>(b, grid, st);
+    if (e != cudaSuccess) return e;
+    if (ws.ev_end && (e = cudaEventRecord(ws.ev_end, st)) != cudaSuccess) return e;
+    ws.main_kernel = tc_kind == kTcBf16 ? "k_tc<bf16>" : "k_tc<fp16>";
+    return cudaSuccess;
 }
 
 bool tc_mode_available(sre_mode_t mode) {

@@ -362,63 +362,81 @@ def tc_mma_flops(N):
     return ((1 << N) - 4096) * tiles * 8 * (2.0 * 128 * 128 * 16)
 
 
-def run_tensor_modes(binding, torch, W, N, fp32_ms, fp32_m2, peaks):
-    """The split-precision tensor-core forms beside the FP32 form: autotuned
-    plans, timed evaluations (after a warm-up) of the same N = 20 state, with
-    the tensor roofline of the executed MMA work."""
+def run_modes(binding, torch, W, N, head_mode, head, peaks):
+    """Every FP32-input arithmetic mode on the benchmark's N = 20 state,
+    side by side: autotuned plan, 3 timed evaluations after a warm-up,
+    the main launch's CUDA-event time (sre_plan_last_kernel_ms), |dM2|
+    against the oracle's golden value, and the roofline of that launch
+    (FP32: algorithmic ops over the FP32 lanes; split modes: executed MMA
+    flops over the measured bf16 peak).  The headline mode's own figures
+    (`head`) are reused instead of measured again."""
     import numpy as np
     psi = torch.from_numpy(W.haar_state(N, W.config_seed(CONFIG_INDEX, 0), np.complex64)).cuda()
     d = 1 << N
-    flops = tc_mma_flops(N)
     ref = golden_m2(N, "complex64")
+    sms = torch.cuda.get_device_properties(psi.device).multi_processor_count
+    alu_peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    peak_s = peaks.get("bf16_tflops_sustained", 1700.0)
+    peak_b = peaks.get("bf16_tflops", 1900.0)
     out = {}
+    for mode in ("fp32", "fp16_split", "bf16_split"):
+        if mode == head_mode:
+            r = dict(head)
+        else:
+            with binding.Plan(N, "c64", mode) as p:
+                tuning, _ = p.autotune(N)
+                p.set_profiling(True)
+                p.m2(psi)
+                torch.cuda.synchronize()
+                kms, walls = [], []
+                for _ in range(3):
+                    t0 = time.perf_counter()
+                    m = p.m2(psi)
+                    walls.append(time.perf_counter() - t0)
+                    kms.append(p.last_kernel_ms()[0])
+                kname = p.last_kernel_ms()[1]
+            r = {"ms": statistics.mean(walls) * 1e3, "kernel_ms": statistics.mean(kms), "kernel": kname,
+                 "m2": m, "tuning": tuning}
+        kms_m = r["kernel_ms"]
+        r["pauli_terms_per_s"] = float(d) * d / (r["ms"] * 1e-3)
+        r["abs_diff_vs_oracle"] = abs(r["m2"] - ref) if ref is not None else None
+        if mode == "fp32":
+            r["alu_roofline_frac"] = (2 * N + 11) * float(d) * (d - 4096) / (kms_m * 1e-3) / alu_peak
+        else:
+            flops = tc_mma_flops(N)
+            r["mma_flops_executed"] = flops
+            r["mma_tflops_executed"] = flops / (kms_m * 1e-3) / 1e12
+            r["tensor_roofline_frac"] = flops / (kms_m * 1e-3) / (peak_s * 1e12)
+            r["tensor_roofline_frac_vs_burst"] = flops / (kms_m * 1e-3) / (peak_b * 1e12)
+        out[mode] = r
     for mode in ("fp16_split", "bf16_split"):
-        with binding.Plan(N, "c64", mode) as p:
-            tuning, _ = p.autotune(N)
-            p.set_profiling(True)
-            p.m2(psi)
-            torch.cuda.synchronize()
-            kms, walls = [], []
-            for _ in range(3):
-                t0 = time.perf_counter()
-                m = p.m2(psi)
-                walls.append(time.perf_counter() - t0)
-                kms.append(p.last_kernel_ms()[0])
-            kms_m = statistics.mean(kms)
-            wall = statistics.mean(walls)
-        peak_s = peaks.get("bf16_tflops_sustained", 1700.0)
-        peak_b = peaks.get("bf16_tflops", 1900.0)
-        out[mode] = {"ms": wall * 1e3, "kernel_ms": kms_m, "pauli_terms_per_s": float(d) * d / wall,
-                     "m2": m, "abs_diff_vs_fp32": abs(m - fp32_m2),
-                     "abs_diff_vs_oracle": abs(m - ref) if ref is not None else None,
-                     "tuning": tuning,
-                     "mma_flops_executed": flops,
-                     "mma_tflops_executed": flops / (kms_m * 1e-3) / 1e12,
-                     "tensor_roofline_frac": flops / (kms_m * 1e-3) / (peak_s * 1e12),
-                     "tensor_roofline_frac_vs_burst": flops / (kms_m * 1e-3) / (peak_b * 1e12),
-                     "vs_fp32_time": (kms_m / fp32_ms) if fp32_ms else None}
-    out["note"] = ("both passes' Hadamard stages as tcgen05 MMAs (pass 1: 4 register bits, one H_128 stage, "
-                   "one accumulator butterfly; pass 2: one H_128 or I x H_{2^h2} stage), fixed-point hi/lo "
-                   "pieces, FP32 accumulate in TMEM; peak = measured bf16 sustained (burst alongside); "
-                   "kernel_ms brackets all kernels of the evaluation")
+        out[mode]["vs_fp32_time"] = out[mode]["ms"] / out["fp32"]["ms"]
+        out[mode]["vs_fp32_kernel_time"] = out[mode]["kernel_ms"] / out["fp32"]["kernel_ms"]
+    out["note"] = ("split modes: both passes' Hadamard stages as tcgen05 MMAs (pass 1: 4 register bits, one "
+                   "H_128 stage, one accumulator butterfly; pass 2: one H_128 or I x H_{2^h2} stage) on "
+                   "fixed-point hi/lo pieces, FP32 accumulate in TMEM; kernel_ms is the launch of the halved "
+                   "shifts x >= 4096 alone; tensor peak = measured bf16 sustained (burst alongside)")
     return out
 
 
-def run_fp64_check(binding, torch, W, N=16):
+def run_fp64_check(binding, torch, W, N=20):
+    """The FP64 path on the complex128 benchmark state at N = 20: one
+    evaluation's time and |dM2| against the oracle's golden value."""
     import numpy as np
-    psi = W.haar_state(N, W.config_seed(2, 1), np.complex128)
+    psi = W.haar_state(N, W.config_seed(CONFIG_INDEX, 0), np.complex128)
     t = torch.from_numpy(psi).cuda()
-    res = {"N": N}
-    for mode in ("fp64", "fp32"):
-        with binding.Plan(N, "c128", mode) as p:
-            p.m2(t)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            m = p.m2(t)
-            res[f"{mode}_ms"] = (time.perf_counter() - t0) * 1e3
-            res[f"m2_{mode}"] = m
-    res["abs_diff_fp32_vs_fp64"] = abs(res["m2_fp32"] - res["m2_fp64"])
-    return res
+    ref = golden_m2(N, "complex128")
+    with binding.Plan(N, "c128", "fp64") as p:
+        p.set_profiling(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = p.m2(t)
+        ms = (time.perf_counter() - t0) * 1e3
+        kms, kname = p.last_kernel_ms()
+    return {"N": N, "dtype": "complex128", "mode": "fp64", "ms": ms, "kernel_ms": kms, "kernel": kname,
+            "m2": m, "abs_diff_vs_oracle": abs(m - ref) if ref is not None else None,
+            "pauli_terms_per_s": float(1 << N) ** 2 / (ms * 1e-3),
+            "note": "one evaluation, no warm-up (default FP64 tuning); tolerance 1e-10"}
 
 
 def run_orders(binding, torch, W, N, fp32_ms, m2_val, orders=(3, 4)):
@@ -687,13 +705,15 @@ def run_gpu(args):
             extras["fp64_check"] = run_fp64_check(binding, torch, W)
         except Exception as exc:
             extras["fp64_check"] = {"error": repr(exc)}
+        head = {"ms": statistics.mean(step_ms), "kernel_ms": statistics.mean(kern_ms), "kernel": kname,
+                "m2": m2_val, "tuning": tuning}
         try:
-            extras["tensor_modes"] = run_tensor_modes(binding, torch, W, N, statistics.mean(kern_ms),
-                                                      m2_val, peaks)
+            extras["modes"] = run_modes(binding, torch, W, N, args.mode, head, peaks)
         except Exception as exc:
-            extras["tensor_modes"] = {"error": repr(exc)}
+            extras["modes"] = {"error": repr(exc)}
         try:
-            extras["orders"] = run_orders(binding, torch, W, N, statistics.mean(kern_ms), m2_val)
+            f32 = extras["modes"].get("fp32") or (head if args.mode == "fp32" else {})
+            extras["orders"] = run_orders(binding, torch, W, N, f32.get("kernel_ms"), f32.get("m2"))
         except Exception as exc:
             extras["orders"] = {"error": repr(exc)}
         try:

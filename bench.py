@@ -54,8 +54,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=30.0)
-    ap.add_argument("--serve-load", type=float, default=0.5)
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="seconds of Poisson arrivals per load point (300 for the 5-minute trace)")
+    ap.add_argument("--serve-loads", default="0.25,0.5,0.75",
+                    help="load points, as fractions of the capacity measured at N = 20")
     ap.add_argument("--batch-states", type=int, default=512)
     return ap.parse_args()
 
@@ -240,72 +242,93 @@ def _serving_trace(rate, seconds, seed, W):
     return trace
 
 
-def run_serving(binding, torch, W, terms_per_s, seconds, load):
-    """Poisson arrivals at `load` x measured capacity through the server, and
-    the same trace with one synchronous launch per request (FIFO)."""
+def _pct(lat, q):
+    return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None
+
+
+def run_serving(binding, torch, W, terms_per_s, seconds, loads, mode, chunk_terms=1 << 37):
+    """Poisson arrivals at each of `loads` x measured capacity: through the
+    server (slots with the autotuned two-pass plans of N = 17..20, large
+    requests split into shift ranges of <= chunk_terms Pauli terms that take
+    turns with the rest), and the same trace with one synchronous launch per
+    request in arrival order (FIFO) on plans created and tuned before its
+    clock starts.  Both arms use the arithmetic mode `mode`."""
     import threading as th
     ns, p = W.serving_n_distribution()
     mean_work = float(sum(pn * 4.0 ** n for n, pn in zip(ns, p)))
     capacity = terms_per_s / mean_work
-    rate = load * capacity
     pool = _serving_pool(torch, W)
-    trace = _serving_trace(rate, seconds, 4242, W)
-    out = {"arrival_rate_per_s": rate, "capacity_per_s": capacity, "load": load,
-           "seconds": seconds, "requests": len(trace), "mean_terms_per_request": mean_work,
-           "n_mix": "P(N) ~ 2^-(N-10)/2, N in 10..20; Haar/product/stabilizer/brickwork"}
-    with binding.Server(max_inflight=4, max_N=20, hbm_budget_bytes=16 << 30) as srv:
+    tunings = {}
+    for n in range(17, 21):
+        with binding.Plan(n, "c64", mode) as pl:
+            tunings[n], _ = pl.autotune(n)
+    # the FIFO arm's plans, tuned the same way, exist before any clock starts
+    plans = {}
+    for n in range(min(ns), max(ns) + 1):
+        plans[n] = binding.Plan(n, "c64", mode)
+        if n in tunings:
+            plans[n].set_tuning(**tunings[n])
+        plans[n].m2(pool[(n, 0)])  # warm-up
+    torch.cuda.synchronize()
+    out = {"capacity_per_s": capacity, "seconds_per_load": seconds, "mean_terms_per_request": mean_work,
+           "mode": mode, "chunk_terms": chunk_terms,
+           "n_mix": "P(N) ~ 2^-(N-10)/2, N in 10..20; Haar/product/stabilizer/brickwork", "loads": {}}
+    for li, load in enumerate(loads):
+        rate = load * capacity
+        trace = _serving_trace(rate, seconds, 4242 + li, W)
+        res = {"arrival_rate_per_s": rate, "requests": len(trace)}
+        with binding.Server(max_inflight=4, max_N=20, hbm_budget_bytes=16 << 30, mode=mode,
+                            slot_scratch_bytes=192 << 20, chunk_terms=chunk_terms) as srv:
+            for n, t in tunings.items():
+                srv.set_tuning(n, t)
+            t0 = time.perf_counter()
+            tickets = []
+            for (ta, n, fam) in trace:
+                dt = t0 + ta - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append(srv.submit(pool[(n, fam)]))
+            for tk in tickets:
+                srv.wait(tk, 600000)
+            st = srv.stats()
+        res["server"] = {k: st[k] for k in ("p50_latency_ms", "p99_latency_ms", "mean_latency_ms",
+                                            "states_per_s", "pauli_terms_per_s", "completed", "failed",
+                                            "rejected", "peak_resident_bytes")}
+        # one launch per request, FIFO, same arrivals
+        lat = []
+        q, lock, done_ev = [], th.Lock(), th.Event()
+
+        def worker():
+            idx = 0
+            while idx < len(trace):
+                with lock:
+                    ready = idx < len(q)
+                if not ready:
+                    time.sleep(0.0002)
+                    continue
+                (ta_abs, n, fam) = q[idx]
+                plans[n].m2(pool[(n, fam)])
+                lat.append((time.perf_counter() - ta_abs) * 1000.0)
+                idx += 1
+            done_ev.set()
+
+        w = th.Thread(target=worker)
+        w.start()
         t0 = time.perf_counter()
-        tickets = []
         for (ta, n, fam) in trace:
             dt = t0 + ta - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            tickets.append(srv.submit(pool[(n, fam)]))
-        for tk in tickets:
-            srv.wait(tk, 600000)
-        st = srv.stats()
-    out["server"] = {k: st[k] for k in ("p50_latency_ms", "p99_latency_ms", "mean_latency_ms",
-                                        "states_per_s", "pauli_terms_per_s", "completed", "failed",
-                                        "rejected", "peak_resident_bytes")}
-    # one launch per request, FIFO, same arrivals
-    lat = []
-    plans = {}
-    q, lock, done_ev = [], th.Lock(), th.Event()
-
-    def worker():
-        idx = 0
-        while idx < len(trace):
             with lock:
-                ready = idx < len(q)
-            if not ready:
-                time.sleep(0.0002)
-                continue
-            (ta_abs, n, fam) = q[idx]
-            pl = plans.get(n)
-            if pl is None:
-                pl = plans[n] = binding.Plan(n, "c64")
-            pl.m2(pool[(n, fam)])
-            lat.append((time.perf_counter() - ta_abs) * 1000.0)
-            idx += 1
-        done_ev.set()
-
-    w = th.Thread(target=worker)
-    w.start()
-    t0 = time.perf_counter()
-    for (ta, n, fam) in trace:
-        dt = t0 + ta - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        with lock:
-            q.append((time.perf_counter(), n, fam))
-    done_ev.wait()
-    w.join()
-    span = max(1e-9, time.perf_counter() - t0)
-    lat.sort()
-    out["one_launch_per_request"] = {
-        "p50_latency_ms": lat[len(lat) // 2] if lat else None,
-        "p99_latency_ms": lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))] if lat else None,
-        "states_per_s": len(lat) / span}
+                q.append((time.perf_counter(), n, fam))
+        done_ev.wait()
+        w.join()
+        span = max(1e-9, time.perf_counter() - t0)
+        lat.sort()
+        res["one_launch_per_request"] = {"p50_latency_ms": _pct(lat, 0.50), "p99_latency_ms": _pct(lat, 0.99),
+                                         "mean_latency_ms": sum(lat) / len(lat) if lat else None,
+                                         "states_per_s": len(lat) / span}
+        out["loads"][f"{load:g}"] = res
     for pl in plans.values():
         pl.close()
     return out
@@ -694,7 +717,7 @@ def run_gpu(args):
     if not args.no_extras:
         try:
             extras["serving"] = run_serving(binding, torch, W, value / world, args.serve_seconds,
-                                            args.serve_load)
+                                            [float(v) for v in args.serve_loads.split(",")], args.mode)
         except Exception as exc:  # reported, not hidden
             extras["serving"] = {"error": repr(exc)}
         try:
@@ -741,9 +764,11 @@ def run_gpu(args):
         "gpu_launches": int(launches), "wall_s": wall,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
     }
-    if extras.get("serving") and "server" in extras["serving"]:
-        line["serve_p50_ms"] = extras["serving"]["server"]["p50_latency_ms"]
-        line["serve_p99_ms"] = extras["serving"]["server"]["p99_latency_ms"]
+    loads = (extras.get("serving") or {}).get("loads") or {}
+    mid = loads.get("0.5") or (next(iter(loads.values())) if loads else None)
+    if mid and "server" in mid:
+        line["serve_p50_ms"] = mid["server"]["p50_latency_ms"]
+        line["serve_p99_ms"] = mid["server"]["p99_latency_ms"]
     line["extras"] = extras
     print(json.dumps(line), flush=True)
     plan.close()

@@ -362,12 +362,22 @@ typedef struct sre_server_s *sre_server_t;
 
 typedef struct {
     uint64_t hbm_budget_bytes; /* admission limit on resident request bytes */
-    int max_inflight;          /* slots: requests on the device at once */
+    int max_inflight;          /* slots: units of work on the device at once */
     int max_queue;             /* waiting requests before SRE_EBUSY */
     int max_N;                 /* largest N accepted */
-    sre_mode_t mode;           /* arithmetic for every request */
+    sre_mode_t mode;           /* arithmetic for every request: FP32, FP64 or a split mode
+                                  (split modes: requests with 16 <= N <= 20 run their halved
+                                  shifts on the tensor cores, merged small requests in FP32) */
     uint64_t wait_limit_ns;    /* bound on every device-side wait */
     int device;                /* CUDA device ordinal */
+    uint64_t slot_scratch_bytes; /* scratch ring of each slot; 0: 96 MiB (room for the
+                                    library's default rings); tuned rings may need more */
+    uint64_t chunk_terms;      /* 0: every request is one unit.  Otherwise a request with
+                                  N > 16 and more than chunk_terms Pauli terms runs as 2^k
+                                  shift ranges of at most chunk_terms terms (at least 4096
+                                  shifts each); the ranges of one request take turns with
+                                  the other queued work, and their partial sums are added
+                                  in range order before the final log */
 } sre_server_cfg_t;
 
 typedef struct {
@@ -379,12 +389,22 @@ typedef struct {
 } sre_server_stats_t;
 
 /* Fill cfg with defaults (HBM budget 8 GiB, 4 slots, 4096 queued,
- * max_N 20, FP32, 5 s wait limit, device 0). */
+ * max_N 20, FP32, 5 s wait limit, device 0, default slot scratch, no
+ * chunking). */
 SRE_API void sre_server_cfg_default(sre_server_cfg_t *cfg);
 
 /* Start a server: a host scheduler thread plus device streams.  *out set
  * on SRE_OK.  Errors: SRE_EINVAL, SRE_ENOMEM, SRE_ECUDA. */
 SRE_API sre_status_t sre_server_create(const sre_server_cfg_t *cfg, sre_server_t *out);
+
+/*
+ * Tuning of the two-pass kernel for requests of N qubits (13 <= N <= the
+ * server's max_N; fields as sre_tuning_t for sre_plan_set_tuning, -1 keeps
+ * the library's choice), applied to the halved shifts of every later unit
+ * of that N.  The ring must fit each slot's scratch (SRE_EINVAL otherwise;
+ * see slot_scratch_bytes).  Thread-safe.
+ */
+SRE_API sre_status_t sre_server_set_tuning(sre_server_t srv, int N, const sre_tuning_t *tuning);
 
 /*
  * Submit one request.  state: interleaved amplitudes of `dtype`, 2^N of

@@ -65,7 +65,8 @@ class Tuning(ctypes.Structure):
 class ServerCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
                 ("max_queue", ctypes.c_int), ("max_N", ctypes.c_int), ("mode", ctypes.c_int),
-                ("wait_limit_ns", ctypes.c_uint64), ("device", ctypes.c_int)]
+                ("wait_limit_ns", ctypes.c_uint64), ("device", ctypes.c_int),
+                ("slot_scratch_bytes", ctypes.c_uint64), ("chunk_terms", ctypes.c_uint64)]
 
 
 class ServerStats(ctypes.Structure):
@@ -113,6 +114,7 @@ def _declare(lib):
         "sre_server_cfg_default": (None, [ctypes.POINTER(ServerCfg)]),
         "sre_server_create": (S, [ctypes.POINTER(ServerCfg), ctypes.POINTER(_vp)]),
         "sre_server_submit": (S, [_vp, _vp, _i, _i, _i, ctypes.POINTER(_u64)]),
+        "sre_server_set_tuning": (S, [_vp, _i, ctypes.POINTER(Tuning)]),
         "sre_server_poll": (S, [_vp, _u64, ctypes.POINTER(_i), _dp]),
         "sre_server_wait": (S, [_vp, _u64, ctypes.c_double, _dp]),
         "sre_server_stats": (S, [_vp, ctypes.POINTER(ServerStats)]),
@@ -443,14 +445,16 @@ class Server:
     """sre_server_t: continuous-batching M2 requests of mixed N."""
 
     def __init__(self, hbm_budget_bytes=None, max_inflight=None, max_queue=None, max_N=None,
-                 mode: str | None = None, wait_limit_ns=None, device=None):
+                 mode: str | None = None, wait_limit_ns=None, device=None, slot_scratch_bytes=None,
+                 chunk_terms=None):
         lib = load_library()
         _torch()
         cfg = ServerCfg()
         lib.sre_server_cfg_default(ctypes.byref(cfg))
         for k, v in (("hbm_budget_bytes", hbm_budget_bytes), ("max_inflight", max_inflight),
                      ("max_queue", max_queue), ("max_N", max_N), ("wait_limit_ns", wait_limit_ns),
-                     ("device", device)):
+                     ("device", device), ("slot_scratch_bytes", slot_scratch_bytes),
+                     ("chunk_terms", chunk_terms)):
             if v is not None:
                 setattr(cfg, k, int(v))
         if mode is not None:
@@ -459,6 +463,12 @@ class Server:
         h = ctypes.c_void_p()
         _check(lib.sre_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sre_server_create")
         self._h = h
+
+    def set_tuning(self, N: int, tuning: dict):
+        """sre_server_set_tuning: two-pass tuning (a dict as Plan.autotune
+        returns; missing fields = library choice) for requests of N qubits."""
+        t = Tuning(*[int(tuning.get(k, -1)) for k, _ in Tuning._fields_])
+        _check(load_library().sre_server_set_tuning(self._h, int(N), ctypes.byref(t)), "sre_server_set_tuning")
 
     def submit(self, state) -> int:
         """Submit a state (CUDA tensor, CPU tensor or numpy array); returns a ticket.

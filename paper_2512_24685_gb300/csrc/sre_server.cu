@@ -49,6 +49,11 @@ struct Request {
     double m2 = 0.0;
     int status = 0;
     bool done = false;
+    // shift-range units (chunked requests have parts > 1)
+    int parts = 1, next_part = 0, parts_done = 0;
+    std::vector<double> S_part;  // partial S of each range
+    double n2 = 0.0;
+    int unit_status = 0;         // first non-zero status of a unit
 };
 
 struct Slot {
@@ -63,6 +68,7 @@ struct Slot {
     sre::Result *h_res = nullptr;  // pinned (single-request path)
     std::vector<uint64_t> tickets;  // in flight
     bool single = false;
+    int part = 0;                   // single path: the unit (shift range) in flight
     bool busy = false;
 };
 
@@ -90,9 +96,21 @@ struct sre_server_s {
     std::map<size_t, std::vector<void *>> pool;  // device buffers by size
     cudaStream_t copy_stream = nullptr;          // submit-side copies / conversions
     std::mutex copy_mu;
+    sre::LargeCfg tuned[SRE_MAX_QUBITS + 1];     // sre_server_set_tuning, per N
+    bool has_tuned[SRE_MAX_QUBITS + 1] = {};
 };
 
 namespace {
+
+// Shift ranges of a request: 2^k ranges of at most chunk_terms Pauli terms
+// each (and at least 4096 shifts) for N > kBatchMaxN, else one.
+int server_parts(const sre_server_cfg_t &cfg, int N) {
+    if (!cfg.chunk_terms || N <= kBatchMaxN) return 1;
+    const double terms = std::ldexp(1.0, 2 * N);
+    int k = 0;
+    while (terms / std::ldexp(1.0, k) > (double)cfg.chunk_terms && N - k > sre::kTileBits) ++k;
+    return 1 << k;
+}
 
 void *pool_get(sre_server_s *s, size_t bytes) {
     auto it = s->pool.find(bytes);
@@ -126,7 +144,39 @@ void finish(sre_server_s *s, Request &r, double m2, int status) {
     s->resident -= r.bytes;
 }
 
-// Launch the next unit of work on slot k (mutex held).
+// A unit of a chunked request has finished (or failed to launch): record
+// its partial sum and finish the request after its last unit, adding the
+// partial sums in range order (Eq. (final1) on their total).
+void unit_done(sre_server_s *s, Request &r, int part, double S, double n2, int status) {
+    if (status && !r.unit_status) r.unit_status = status;
+    if (status == SRE_ECUDA || status == SRE_ETIMEDOUT) {
+        // drop the units not launched yet
+        r.parts_done += r.parts - r.next_part;
+        r.next_part = r.parts;
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+            if (*it == r.ticket) {
+                s->queue.erase(it);
+                break;
+            }
+    }
+    if (part >= 0) {
+        r.S_part[(size_t)part] = S;
+        r.n2 = n2;
+    }
+    r.parts_done += 1;
+    if (r.parts_done < r.parts) return;
+    double St = 0.0;
+    for (double v : r.S_part) St += v;
+    const int st = r.unit_status;
+    const double m2 = (st || !(St > 0.0) || !(r.n2 > 0.0)) ? std::nan("")
+                                                           : -(std::log2(St) - (double)r.N - 4.0 * std::log2(r.n2));
+    finish(s, r, m2, st);
+}
+
+// Launch the next unit of work on slot sl (mutex held): the oldest queued
+// request, merged with later small requests, or one shift range of a large
+// (possibly chunked) request, which then goes to the back of the queue if
+// it has more ranges.
 void launch_unit(sre_server_s *s, Slot &sl) {
     if (s->queue.empty()) return;
     std::vector<uint64_t> take;
@@ -134,7 +184,8 @@ void launch_unit(sre_server_s *s, Slot &sl) {
     Request &h = s->reqs[head];
     s->queue.pop_front();
     take.push_back(head);
-    if (h.N <= kBatchMaxN) {
+    const bool single = h.N > kBatchMaxN;
+    if (!single) {
         double work = std::ldexp(1.0, 2 * h.N);
         for (auto it = s->queue.begin(); it != s->queue.end() && (int)take.size() < kBatchMaxCount;) {
             const Request &q = s->reqs[*it];
@@ -150,10 +201,20 @@ void launch_unit(sre_server_s *s, Slot &sl) {
     }
     const sre_dtype_t dt = s->cfg.mode == SRE_MODE_FP64 ? SRE_C128 : SRE_C64;
     cudaError_t e;
-    sl.single = take.size() == 1 && h.N > kBatchMaxN;
-    if (sl.single) {
-        e = sre::enqueue_m2(sl.ws, s->dev, h.d_state, dt, h.N, 0, 1ull << h.N, s->cfg.mode, sl.stream,
-                            nullptr, nullptr, (long long)s->cfg.wait_limit_ns, nullptr);
+    sl.single = single;
+    if (single) {
+        const int part = h.next_part++;
+        if (h.next_part < h.parts) s->queue.push_back(head);  // round robin over ranges
+        const uint64_t d = 1ull << h.N, span = d / (uint64_t)h.parts;
+        sre::LargeCfg c;
+        sre::LargeCfg *cp = nullptr;
+        if (s->has_tuned[h.N]) {
+            c = s->tuned[h.N];
+            cp = &c;
+        }
+        sl.part = part;
+        e = sre::enqueue_m2(sl.ws, s->dev, h.d_state, dt, h.N, span * (uint64_t)part, span * (uint64_t)(part + 1),
+                            s->cfg.mode, sl.stream, nullptr, nullptr, (long long)s->cfg.wait_limit_ns, cp);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(sl.h_res, sl.ws.result, sizeof(sre::Result), cudaMemcpyDeviceToHost, sl.stream);
     } else {
@@ -175,10 +236,13 @@ void launch_unit(sre_server_s *s, Slot &sl) {
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        for (uint64_t t : take) finish(s, s->reqs[t], std::nan(""), SRE_ECUDA);
+        if (single)
+            unit_done(s, h, -1, 0.0, 0.0, SRE_ECUDA);
+        else
+            for (uint64_t t : take) finish(s, s->reqs[t], std::nan(""), SRE_ECUDA);
         return;
     }
-    s->admitted += take.size();
+    if (!single || sl.part == 0) s->admitted += take.size();
     sl.tickets = take;
     sl.busy = true;
 }
@@ -189,10 +253,15 @@ void collect(sre_server_s *s, Slot &sl) {
     if (q != cudaSuccess) cudaGetLastError();
     for (size_t i = 0; i < sl.tickets.size(); ++i) {
         Request &r = s->reqs[sl.tickets[i]];
-        if (q != cudaSuccess) {
+        if (sl.single) {
+            if (q != cudaSuccess)
+                unit_done(s, r, -1, 0.0, 0.0, SRE_ECUDA);
+            else if (r.parts == 1)
+                finish(s, r, sl.h_res->m2, sl.h_res->status);  // the device's own M2, as alone
+            else
+                unit_done(s, r, sl.part, sl.h_res->S, sl.h_res->n2, sl.h_res->status);
+        } else if (q != cudaSuccess) {
             finish(s, r, std::nan(""), SRE_ECUDA);
-        } else if (sl.single) {
-            finish(s, r, sl.h_res->m2, sl.h_res->status);
         } else {
             finish(s, r, sl.h_out[i], sl.h_st[i]);
         }
@@ -256,13 +325,17 @@ void sre_server_cfg_default(sre_server_cfg_t *cfg) {
     cfg->mode = SRE_MODE_FP32;
     cfg->wait_limit_ns = 5000000000ull;
     cfg->device = 0;
+    cfg->slot_scratch_bytes = 0;
+    cfg->chunk_terms = 0;
 }
 
 sre_status_t sre_server_create(const sre_server_cfg_t *cfg, sre_server_t *out) {
     if (!cfg || !out) return SRE_EINVAL;
     if (cfg->max_N < 1 || cfg->max_N > SRE_MAX_QUBITS || cfg->max_inflight < 1 || cfg->max_inflight > 64 ||
-        cfg->max_queue < 1 || (cfg->mode != SRE_MODE_FP32 && cfg->mode != SRE_MODE_FP64))
+        cfg->max_queue < 1 ||
+        (cfg->mode != SRE_MODE_FP32 && cfg->mode != SRE_MODE_FP64 && !sre::tc_mode_available(cfg->mode)))
         return SRE_EINVAL;
+    if (cfg->slot_scratch_bytes > (64ull << 30)) return SRE_EINVAL;
     if (cudaSetDevice(cfg->device) != cudaSuccess) {
         cudaGetLastError();
         return SRE_ECUDA;
@@ -283,7 +356,8 @@ sre_status_t sre_server_create(const sre_server_cfg_t *cfg, sre_server_t *out) {
     s->slots.resize(cfg->max_inflight);
     for (Slot &sl : s->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = sre::workspace_alloc(&sl.ws, s->dev, cfg->max_N, eb, cfg->mode, sre::kSlotScratch);
+        const size_t scratch = cfg->slot_scratch_bytes ? (size_t)cfg->slot_scratch_bytes : sre::kSlotScratch;
+        if (e == cudaSuccess) e = sre::workspace_alloc(&sl.ws, s->dev, cfg->max_N, eb, cfg->mode, scratch);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_out, sizeof(double) * kBatchMaxCount);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, sizeof(double) * kBatchMaxCount);
@@ -311,6 +385,27 @@ sre_status_t sre_server_create(const sre_server_cfg_t *cfg, sre_server_t *out) {
     }
     s->worker = std::thread(worker_main, s);
     *out = s;
+    return SRE_OK;
+}
+
+sre_status_t sre_server_set_tuning(sre_server_t s, int N, const sre_tuning_t *t) {
+    if (!s || !t || N <= sre::kTileBits || N > s->cfg.max_N) return SRE_EINVAL;
+    const int eb = s->cfg.mode == SRE_MODE_FP64 ? 16 : 8;
+    sre::LargeCfg c = sre::choose_large_cfg(s->dev, N, eb, 1);
+    if (t->x_batch_log >= 0) c.C_log = t->x_batch_log;
+    if (t->ring_slots >= 0) c.R = t->ring_slots;
+    if (t->lag >= 0) c.D = t->lag;
+    if (t->pass2_tiles_log >= 0) c.G2_log = t->pass2_tiles_log;
+    if (t->pass1_blocks_log >= 0) c.B1_log = t->pass1_blocks_log;
+    if (t->pass1_staged >= 0) c.stage1 = t->pass1_staged;
+    if (t->pass2_staged >= 0) c.stage2 = t->pass2_staged;
+    c.G2_log = std::min(c.G2_log, N - sre::kTileBits - 1);
+    c.B1_log = std::min(c.B1_log, N - sre::kTileBits - 1);
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (const Slot &sl : s->slots)
+        if (!sre::large_cfg_fits(sl.ws, c, N, 1)) return SRE_EINVAL;
+    s->tuned[N] = c;
+    s->has_tuned[N] = true;
     return SRE_OK;
 }
 
@@ -367,6 +462,8 @@ sre_status_t sre_server_submit(sre_server_t s, const void *state, int on_device,
     r.N = N;
     r.d_state = d;
     r.bytes = bytes;
+    r.parts = server_parts(s->cfg, N);
+    r.S_part.assign((size_t)r.parts, 0.0);
     r.t_submit = Clock::now();
     if (!s->have_first) {
         s->t_first = r.t_submit;

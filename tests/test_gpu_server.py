@@ -155,3 +155,52 @@ def test_server_merged_batch_reports_device_timeout(sre, torch_cuda):
     # the server stays usable with an ordinary limit afterwards
     with sre.Server(max_inflight=1, max_N=16) as srv:
         assert abs(srv.wait(srv.submit(states[0]), 60000) - oracle.m2(states[0])) <= 1e-6
+
+
+def test_server_chunked_requests_and_tuning(sre, torch_cuda):
+    """Requests with N > 16 split into shift ranges (chunk_terms) come back
+    with the M2 of the whole state (partial sums added in range order), and
+    a tuning set for an N applies to its units; a ring larger than the
+    slot scratch is refused."""
+    torch = torch_cuda
+    Ns = [18, 12, 17, 10, 18, 14, 17]
+    states = [W.haar_state(n, 700 + k, np.complex64) for k, n in enumerate(Ns)]
+    alone = []
+    for v in states:
+        with sre.Plan(v.size.bit_length() - 1, "c64") as p:
+            alone.append(p.m2(torch.from_numpy(v).cuda()))
+    with sre.Plan(18, "c64") as p:
+        tun18, _ = p.autotune(18)
+    with sre.Server(max_inflight=3, max_N=18, chunk_terms=1 << 33,
+                    slot_scratch_bytes=256 << 20) as srv:
+        srv.set_tuning(18, tun18)
+        with pytest.raises(sre.SreError) as e:
+            srv.set_tuning(18, {"x_batch_log": 3, "ring_slots": 47, "lag": 5})  # 394 MB ring
+        assert e.value.status == 1
+        tickets = [srv.submit(v) for v in states]
+        got = [srv.wait(t, 120000) for t in tickets]
+        st = srv.stats()
+    for n, g, a, v in zip(Ns, got, alone, states):
+        assert abs(g - a) <= 1e-9, (n, g, a)
+        if n <= 14:
+            assert abs(g - oracle.m2(v)) <= 1e-6
+    assert st["completed"] == len(Ns) and st["failed"] == 0 and st["admitted"] == len(Ns)
+
+
+def test_server_split_mode(sre, torch_cuda):
+    """A server in the FP16 split mode: N = 17 requests take the tensor-core
+    kernel (bitwise the plan's result in that mode), small ones the merged
+    FP32 launches."""
+    torch = torch_cuda
+    states = [W.haar_state(17, 811, np.complex64), W.haar_state(11, 812, np.complex64),
+              W.haar_state(17, 813, np.complex64)]
+    want = []
+    for v in states:
+        n = v.size.bit_length() - 1
+        with sre.Plan(n, "c64", "fp16_split" if n == 17 else "fp32") as p:
+            want.append(p.m2(torch.from_numpy(v).cuda()))
+    with sre.Server(max_inflight=2, max_N=17, mode="fp16_split") as srv:
+        got = [srv.wait(srv.submit(v), 120000) for v in states]
+    for g, w in zip(got, want):
+        assert abs(g - w) <= 1e-12, (g, w)
+    assert abs(got[1] - oracle.m2(states[1])) <= 1e-6

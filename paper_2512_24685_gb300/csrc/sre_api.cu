@@ -309,37 +309,52 @@ sre_status_t sre_plan_autotune(sre_plan_t p, int N, sre_stream_t stream, sre_tun
     const int eb = elem_bytes_for_mode(p->mode);
     const sre::LargeCfg base = sre::choose_large_cfg(p->dev, N, eb, 1);
     const int h2 = N - sre::kTileBits - 1;
+    // the tensor-core kernel runs one CTA per SM and always stages its
+    // copies, so its lag steps are counted over the SMs, its lag is tried at
+    // every step count, and the copy-path fields are not varied
+    const bool tc = sre::tc_mode_available(p->mode) && sre::tc_applies(N, 1, 2, p->tune_state);
+    const int grid_eff = tc ? std::min(base.grid, p->dev.sms) : base.grid;
     std::vector<sre::LargeCfg> cands;
     auto add = [&](const sre::LargeCfg &c) {
         for (const sre::LargeCfg &o : cands)
             if (o.C_log == c.C_log && o.G2_log == c.G2_log && o.B1_log == c.B1_log && o.D == c.D &&
-                o.stage1 == c.stage1 && o.stage2 == c.stage2)
+                o.R == c.R && o.stage1 == c.stage1 && o.stage2 == c.stage2)
                 return;
         if (sre::large_cfg_fits(p->ws, c, N, 1)) cands.push_back(c);
     };
     for (int C_log = 0; C_log <= 3; ++C_log)
         for (int g = 0; g <= 3; ++g)
             for (int b = 2; b <= 3; ++b)
-                for (int dm = 0; dm <= 3; ++dm) {
+                for (int dm = 0; dm <= (tc ? 6 : 3); ++dm) {
                     sre::LargeCfg c = base;
                     c.C_log = C_log;
                     c.G2_log = std::min(h2, C_log + g);
                     c.B1_log = std::min(h2, std::max(0, b - C_log));
                     const int P1 = 1 << (h2 - c.B1_log);
                     const int P2 = (1 << C_log) << (h2 - c.G2_log);
-                    const int steps = std::max(1, (base.grid + P1 + P2 - 1) / (P1 + P2));
+                    const int steps = std::max(1, (grid_eff + P1 + P2 - 1) / (P1 + P2));
                     // ring of 2 D + 1 chunks, or as many as the scratch holds
                     // (at least D + 2)
                     const size_t per_chunk = ((size_t)eb << (N - 1)) << C_log;
                     const int r_fit = (int)std::min<size_t>(p->ws.scratch_bytes / per_chunk, sre::kMaxRing);
-                    c.D = std::min(dm > 0 ? dm * steps + 1 : (r_fit - 1) / 2, sre::kMaxRing / 2 - 1);
+                    // tensor-core kernel: D = steps * (dm + 1) / 2 + 1 for dm = 1..6,
+                    // i.e. every half step from one to 3.5 lag steps
+                    const int dd = tc ? (steps * (dm + 1)) / 2 + 1 : dm * steps + 1;
+                    c.D = std::min(dm > 0 ? dd : (r_fit - 1) / 2, sre::kMaxRing / 2 - 1);
                     if (c.D < 1) continue;
                     c.R = std::min(2 * c.D + 1, r_fit);
                     if (c.R < c.D + 2) continue;
+                    if (tc && c.R < r_fit) {
+                        // the tensor-core kernel also tries the largest ring
+                        sre::LargeCfg w = c;
+                        w.R = r_fit;
+                        w.stage1 = w.stage2 = 1;
+                        add(w);
+                    }
                     // both copy paths where they apply
                     const bool tma = eb == 8 && h2 >= 5 && h2 <= 8;
-                    for (int s1 = (C_log == 0 && eb == 8) ? 0 : 1; s1 <= 1; ++s1)
-                        for (int s2 = tma ? 0 : 1; s2 <= 1; ++s2) {
+                    for (int s1 = (C_log == 0 && eb == 8 && !tc) ? 0 : 1; s1 <= 1; ++s1)
+                        for (int s2 = (tma && !tc) ? 0 : 1; s2 <= 1; ++s2) {
                             c.stage1 = s1;
                             c.stage2 = s2;
                             add(c);

@@ -328,7 +328,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                     for (int kb = 0; kb < (1 << a.B1_log); ++kb) {
                         const int th = tc_block((it.r << a.B1_log) + kb, jh);
                         const int uq = take_unit(), up = take_unit();
-                        fence_proxy_async();
+                        // the units' earlier readers (generic loads of the compute
+                        // warps, or MMAs) come before the copies' writes
+                        fence_proxy_async_smem();
                         const uint32_t fq = smem_u32(&sh.u_full1[uq]), fp = smem_u32(&sh.u_full1[up]);
                         f1 ^= (1u << uq) | (1u << up);
                         p1used |= (1u << uq) | (1u << up);
@@ -344,10 +346,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                     const int zb0 = (it.r & ((1 << ipx_log) - 1)) << a.G2_log;
                     const int y_hi = (int)((((size_t)it.slot * C + xl) * 2) << H2);
                     wait_counter(a.done1 + it.chunk, (unsigned)(a.P1 * 4), a.status, a.wait_ns);
+                    // the chunk's scratch rows (generic stores of other CTAs,
+                    // acquired above) come before the TMA reads
                     fence_proxy_async();
                     for (int g = 0; g < (1 << a.G2_log); ++g) {
                         const int u = take_unit();
-                        fence_proxy_async();
+                        fence_proxy_async_smem();
                         const uint32_t f = smem_u32(&sh.u_full2[u]);
                         f2 ^= 1u << u;
                         p2used |= 1u << u;

@@ -334,17 +334,19 @@ def run_serving(binding, torch, W, terms_per_s, seconds, loads, mode, chunk_term
     return out
 
 
-def run_batched(binding, torch, W, count):
+def run_batched(binding, torch, W, count, mode="fp32"):
     """The uneven batched workload: `count` brickwork states, N ~ U{12..18},
-    depth ~ U{1..32}, one sre_m2_batched submission replayed from its graph."""
+    depth ~ U{1..32}, one sre_m2_batched submission replayed from its graph,
+    in arithmetic mode `mode` (split modes: the N = 16..18 classes on the
+    tensor cores)."""
     spec = W.uneven_batch_spec(count=count)
     states = [W.brickwork_state_torch(n, t, s, "cuda", dtype=torch.complex64).contiguous()
               for n, t, s in spec]
     terms = float(sum(4.0 ** n for n, _, _ in spec))
     side = torch.cuda.Stream()
     torch.cuda.synchronize()
-    with binding.Plan(18, "c64") as plan, torch.cuda.stream(side):
-        for n in (18, 17):
+    with binding.Plan(18, "c64", mode) as plan, torch.cuda.stream(side):
+        for n in ((18, 17, 16) if mode != "fp32" else (18, 17)):
             plan.autotune(n)
         out = torch.empty(count, dtype=torch.float64, device="cuda")
         plan.m2_batched(states, out=out)  # eager run + graph capture
@@ -360,7 +362,8 @@ def run_batched(binding, torch, W, count):
         launches = plan.launch_count() - l0
     return {"states": count, "pauli_terms": terms, "ms": ms, "states_per_s": count / (ms / 1e3),
             "pauli_terms_per_s": terms / (ms / 1e3), "gpu_launches": launches,
-            "workload": "brickwork Haar circuits on |0^N>, N ~ U{12..18}, depth ~ U{1..32}, complex64, FP32"}
+            "mode": mode,
+            "workload": "brickwork Haar circuits on |0^N>, N ~ U{12..18}, depth ~ U{1..32}, complex64"}
 
 
 def golden_m2(N, dtype_name):
@@ -720,10 +723,12 @@ def run_gpu(args):
                                             [float(v) for v in args.serve_loads.split(",")], args.mode)
         except Exception as exc:  # reported, not hidden
             extras["serving"] = {"error": repr(exc)}
-        try:
-            extras["batched"] = run_batched(binding, torch, W, args.batch_states)
-        except Exception as exc:
-            extras["batched"] = {"error": repr(exc)}
+        for bmode in ("fp32", "fp16_split"):
+            key = "batched" if bmode == "fp32" else f"batched_{bmode}"
+            try:
+                extras[key] = run_batched(binding, torch, W, args.batch_states, bmode)
+            except Exception as exc:
+                extras[key] = {"error": repr(exc)}
         try:
             extras["fp64_check"] = run_fp64_check(binding, torch, W)
         except Exception as exc:

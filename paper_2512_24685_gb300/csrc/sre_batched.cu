@@ -67,6 +67,9 @@ struct BatchedContext {
     size_t flags_cap = 0;
     unsigned *counters = nullptr;
     size_t counters_cap = 0;  // 3 * chunk capacity
+    int *tc_e = nullptr;      // split modes: per-state scale tables of a class
+    double *tc_bn = nullptr;
+    size_t tc_e_cap = 0, tc_bn_cap = 0;
     unsigned long long generation = 1;
     std::vector<GraphEntry> graphs;  // most recent last
 };
@@ -94,6 +97,8 @@ void batched_destroy(BatchedContext *ctx) {
     cudaFree(ctx->npart);
     cudaFree(ctx->flags);
     cudaFree(ctx->counters);
+    cudaFree(ctx->tc_e);
+    cudaFree(ctx->tc_bn);
     delete ctx;
 }
 
@@ -123,7 +128,8 @@ static cudaError_t enqueue_entry(BatchedContext *ctx, const Workspace &ws, const
     size_t first = 0;
     for (const BatchClass &L : classes) {
         if ((e = enqueue_batch_class(ws, dev, L, g.d_ptrs + first, ctx->parts, ctx->counters, chunk_cap,
-                                     g.mode, st, wait_ns)) != cudaSuccess)
+                                     g.mode, st, wait_ns, ctx->tc_e, ctx->tc_bn,
+                                     std::min(ctx->tc_e_cap, ctx->tc_bn_cap))) != cudaSuccess)
             return e;
         first += (size_t)L.S;
     }
@@ -225,6 +231,35 @@ cudaError_t batched_run(BatchedContext *ctx, const Workspace &ws, const DeviceIn
     for (int k = 0; k < count; ++k) {
         sptr[k] = convert ? (const void *)((char *)g.conv + off) : d_states[order[k]];
         if (convert) off += (size_t)(fp64 ? 16 : 8) << sNs[k];
+    }
+    // split modes: a class whose halved shifts fit the tensor-core kernel
+    // (16 <= N <= 20) and whose states are all 16-byte aligned takes it
+    {
+        size_t tc_need = 0;
+        int k = 0;
+        for (BatchClass &L : classes) {
+            L.tc_kind = 0;
+            if (tc_mode_available(mode) && L.N > kTileBits && tc_applies(L.N, 1, 2, sptr[k])) {
+                bool aligned = true;
+                for (int q = 0; q < L.S; ++q) aligned &= ((uintptr_t)sptr[k + q] & 15) == 0;
+                if (aligned) {
+                    L.tc_kind = mode == SRE_MODE_BF16_SPLIT ? 1 : 2;
+                    tc_need = std::max(tc_need, (size_t)L.S << (L.N - kTileBits));
+                }
+            }
+            k += L.S;
+        }
+        const size_t tc0 = ctx->tc_e_cap + ctx->tc_bn_cap;
+        if (tc_need && ((e = grow(&ctx->tc_e, &ctx->tc_e_cap, tc_need)) != cudaSuccess ||
+                        (e = grow(&ctx->tc_bn, &ctx->tc_bn_cap, tc_need)) != cudaSuccess)) {
+            free_entry(g);
+            ctx->graphs.pop_back();
+            return e;
+        }
+        if (ctx->tc_e_cap + ctx->tc_bn_cap != tc0) {
+            ++ctx->generation;  // graphs captured before hold the old tables
+            g.generation = ctx->generation;
+        }
     }
     size_t tmp = 0;
     if ((e = grow(&g.d_ptrs, &tmp, (size_t)count)) != cudaSuccess ||

@@ -92,8 +92,12 @@ LargeCfg choose_large_cfg(const DeviceInfo &dev, int N, int elem_bytes, int half
 // ws.tc_bn / ws.tc_e.
 struct LargeArgs;
 bool tc_applies(int N, int half, int alpha, const void *psi);
+// Tensor-core launch of the halved shifts of one state (a.psi) or of the
+// states of a batch class (a.psis, a.chunks_per_state); the per-state scale
+// tables go to e_buf / bn_buf (buf_cap entries) when given, else to ws.
 cudaError_t launch_large_tc(const LargeArgs &a, const Workspace &ws, const DeviceInfo &dev, int grid,
-                            cudaStream_t st, int tc_kind);
+                            cudaStream_t st, int tc_kind, int *e_buf = nullptr, double *bn_buf = nullptr,
+                            size_t buf_cap = 0);
 
 // Does a (possibly tuned) configuration fit the workspace allocation?
 bool large_cfg_fits(const Workspace &ws, const LargeCfg &c, int N, int half);
@@ -126,6 +130,7 @@ struct BatchClass {
     long long cps_full = 0, cps_half = 0;  // chunks per state of each part
     size_t parts_off = 0, parts_n = 0;     // partials of the class
     size_t chunks_max = 0;                 // counters needed by one launch
+    int tc_kind = 0;                       // split modes: the halved shifts on the tensor cores
 };
 
 BatchClass batch_class_layout(const DeviceInfo &dev, const Workspace &ws, int N, int S,
@@ -133,7 +138,8 @@ BatchClass batch_class_layout(const DeviceInfo &dev, const Workspace &ws, int N,
 cudaError_t enqueue_batch_class(const Workspace &ws, const DeviceInfo &dev, const BatchClass &L,
                                 const void *const *d_ptrs, double *parts, unsigned *counters,
                                 size_t chunk_cap, sre_mode_t mode, cudaStream_t st,
-                                long long wait_ns);
+                                long long wait_ns, int *tc_e = nullptr, double *tc_bn = nullptr,
+                                size_t tc_cap = 0);
 cudaError_t enqueue_batch_norm(const Workspace &ws, const void *const *d_ptrs, const int *d_Ns,
                                int count, double *npart, int *flags, sre_mode_t mode,
                                cudaStream_t st);

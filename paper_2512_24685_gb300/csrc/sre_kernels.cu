@@ -797,7 +797,8 @@ template <typename R>
 static cudaError_t enqueue_batch_class_t(const Workspace &ws, const DeviceInfo &dev,
                                          const BatchClass &L, const void *const *d_ptrs,
                                          double *parts, unsigned *counters, size_t chunk_cap,
-                                         cudaStream_t st, long long wait_ns) {
+                                         cudaStream_t st, long long wait_ns, int *tc_e, double *tc_bn,
+                                         size_t tc_cap) {
     cudaError_t e;
     const int N = L.N;
     if (N <= kTileBits) {
@@ -859,7 +860,10 @@ static cudaError_t enqueue_batch_class_t(const Workspace &ws, const DeviceInfo &
         if ((e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * 3 * chunk_cap, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(ws.work, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
         const int grid = (int)std::max<long long>(1, std::min<long long>(c.grid, A.n_items));
-        e = half ? launch_large<R, true>(A, grid, st) : launch_large<R, false>(A, grid, st);
+        if (half && L.tc_kind)
+            e = launch_large_tc(A, ws, dev, grid, st, L.tc_kind, tc_e, tc_bn, tc_cap);
+        else
+            e = half ? launch_large<R, true>(A, grid, st) : launch_large<R, false>(A, grid, st);
         if (e != cudaSuccess) return e;
         ws.launches += 1;
         off += (size_t)A.n_chunks;
@@ -870,10 +874,12 @@ static cudaError_t enqueue_batch_class_t(const Workspace &ws, const DeviceInfo &
 cudaError_t enqueue_batch_class(const Workspace &ws, const DeviceInfo &dev, const BatchClass &L,
                                 const void *const *d_ptrs, double *parts, unsigned *counters,
                                 size_t chunk_cap, sre_mode_t mode, cudaStream_t st,
-                                long long wait_ns) {
+                                long long wait_ns, int *tc_e, double *tc_bn, size_t tc_cap) {
     if (mode == SRE_MODE_FP64)
-        return enqueue_batch_class_t<double>(ws, dev, L, d_ptrs, parts, counters, chunk_cap, st, wait_ns);
-    return enqueue_batch_class_t<float>(ws, dev, L, d_ptrs, parts, counters, chunk_cap, st, wait_ns);
+        return enqueue_batch_class_t<double>(ws, dev, L, d_ptrs, parts, counters, chunk_cap, st, wait_ns, nullptr,
+                                             nullptr, 0);
+    return enqueue_batch_class_t<float>(ws, dev, L, d_ptrs, parts, counters, chunk_cap, st, wait_ns, tc_e, tc_bn,
+                                        tc_cap);
 }
 
 cudaError_t enqueue_batch_norm(const Workspace &ws, const void *const *d_ptrs, const int *d_Ns,

@@ -63,25 +63,32 @@ constexpr int kTcMinH2 = 3, kTcMaxH2 = 7;
 
 // ----------------------------------------------------------- scale table
 
-// l2 norm of every 4096-entry block of psi (FP64).
+// l2 norm of every 4096-entry block of psi (FP64); blockIdx.y selects the
+// state of a batch class (psis), whose nb = gridDim.x norms follow those of
+// the state before.
 __global__ void __launch_bounds__(kThreads) k_tc_block_norms(const float2 *__restrict__ psi,
+                                                             const void *const *psis,
                                                              double *__restrict__ bn) {
     __shared__ double red[kThreads / 32];
-    const float2 *p = psi + ((size_t)blockIdx.x << kTileBits);
+    const float2 *base = psis ? reinterpret_cast<const float2 *>(psis[blockIdx.y]) : psi;
+    const float2 *p = base + ((size_t)blockIdx.x << kTileBits);
     double s = 0.0;
     for (int t = threadIdx.x; t < kTile; t += kThreads) {
         const float2 v = p[t];
         s += (double)v.x * v.x + (double)v.y * v.y;
     }
     const double b = block_sum(s, red);
-    if (threadIdx.x == 0) bn[blockIdx.x] = sqrt(b);
+    if (threadIdx.x == 0) bn[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = sqrt(b);
 }
 
 // E[x_h] for x_h in [1, nb): ceil(log2(max over blocks b with pivot bit 0 of
 // n(b) n(b ^ x_h), times 1 + 2^-10)); -100 where every product is zero.
-__global__ void k_tc_scales(const double *__restrict__ bn, int nb, int *__restrict__ E) {
+// blockIdx.y selects the state (nb entries of bn and of E per state).
+__global__ void k_tc_scales(const double *__restrict__ bn_all, int nb, int *__restrict__ E_all) {
     const int xh = blockIdx.x * blockDim.x + threadIdx.x;
     if (xh >= nb) return;
+    const double *bn = bn_all + (size_t)blockIdx.y * nb;
+    int *E = E_all + (size_t)blockIdx.y * nb;
     if (xh == 0) {
         E[0] = 0;
         return;
@@ -229,7 +236,7 @@ __device__ __forceinline__ TcItem tc_item(const LargeArgs &a, long long item) {
     }
     t.xc = a.x0 + ((uint64_t)cl << a.C_log);
     t.xh = t.xc >> kTileBits;
-    t.E = a.tc_e[t.xh];
+    t.E = a.tc_e[((size_t)(t.chunk / a.chunks_per_state) << (a.N - kTileBits)) + t.xh];
     const int C = 1 << a.C_log;
     int f = 0;
     while (f < C && !(t.xc + (uint64_t)f >= a.x_begin && t.xc + (uint64_t)f < a.x_end)) ++f;
@@ -863,18 +870,26 @@ bool tc_applies(int N, int half, int alpha, const void *psi) {
 }
 
 cudaError_t launch_large_tc(const LargeArgs &a, const Workspace &ws, const DeviceInfo &dev, int grid,
-                            cudaStream_t st, int tc_kind) {
-    if (a.psis || !a.half || a.alpha != 2) return cudaErrorInvalidValue;
+                            cudaStream_t st, int tc_kind, int *e_buf, double *bn_buf, size_t buf_cap) {
+    if (!a.half || a.alpha != 2) return cudaErrorInvalidValue;
     const int nb = 1 << (a.N - kTileBits);
-    if (!ws.tc_e || !ws.tc_bn || nb > ws.tc_cap) return cudaErrorInvalidValue;
-    k_tc_block_norms<<<nb, kThreads, 0, st>>>(reinterpret_cast<const float2 *>(a.psi), ws.tc_bn);
+    // states of the launch: one, or the states of a batch class
+    const long long S = a.psis ? a.n_chunks / a.chunks_per_state : 1;
+    if (S < 1 || S > 65535 || (a.psis && S * a.chunks_per_state != a.n_chunks)) return cudaErrorInvalidValue;
+    int *tc_e = e_buf ? e_buf : ws.tc_e;
+    double *tc_bn = e_buf ? bn_buf : ws.tc_bn;
+    const size_t cap = e_buf ? buf_cap : (size_t)ws.tc_cap;
+    if (!tc_e || !tc_bn || (size_t)S * nb > cap) return cudaErrorInvalidValue;
+    k_tc_block_norms<<<dim3(nb, (unsigned)S), kThreads, 0, st>>>(reinterpret_cast<const float2 *>(a.psi), a.psis,
+                                                                 tc_bn);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_tc_scales<<<(nb + 127) / 128, 128, 0, st>>>(ws.tc_bn, nb, ws.tc_e);
+    k_tc_scales<<<dim3((nb + 127) / 128, (unsigned)S), 128, 0, st>>>(tc_bn, nb, tc_e);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ws.launches += 2;
     LargeArgs b = a;
-    b.tc_e = ws.tc_e;
+    b.tc_e = tc_e;
+    if (!b.psis) b.chunks_per_state = b.n_chunks;  // one state: every chunk is state 0
     grid = std::max(1, std::min(grid, dev.sms));  // one CTA per SM (all of TMEM)
     if (tc_kind != kTcBf16 && tc_kind != kTcFp16) return cudaErrorInvalidValue;
     // the profiling events bracket the tensor-core kernel alone

@@ -143,3 +143,27 @@ def test_uneven_batch_workload_sample(sre, torch_cuda):
     for k in range(0, 40, 7):
         assert abs(got[k] - oracle.m2(states[k])) <= 1e-6
     assert np.all(np.isfinite(got)) and np.all(got >= -1e-6)
+
+
+@pytest.mark.parametrize("mode", ["fp16_split", "bf16_split"])
+def test_split_mode_batch(sre, torch_cuda, mode):
+    """Split modes in a batch: the N = 16..18 classes take the tensor-core
+    kernel with per-state scale tables; every result equals the state's
+    single evaluation in the same mode bit for bit, and the oracle within
+    1e-6; a replay from the captured graph gives the same values."""
+    torch = torch_cuda
+    spec = [(17, 12, 21), (12, 4, 22), (16, 9, 23), (18, 14, 24), (16, 3, 25), (14, 5, 26), (17, 2, 27),
+            (16, 16, 28)]
+    states = mixed_states(spec)
+    ts = [dev(torch, v) for v in states]
+    with sre.Plan(18, "c64", mode) as p:
+        out = p.m2_batched(ts)
+        torch.cuda.synchronize()
+        first = out.cpu().numpy().copy()
+        again = p.m2_batched(ts).cpu().numpy()
+        singles = [p.m2(t) for t in ts]
+    for v, g, s, r in zip(states, first, singles, again):
+        assert g == s, (v.size, g, s)
+        assert r == g
+        if v.size <= 1 << 16:
+            assert abs(g - oracle.m2(v)) <= 1e-6, (v.size, g)

@@ -52,10 +52,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extras", default="all",
+                    help="comma list of extras to run: serving, batched, batched_fp16_split, fp64_check, "
+                         "modes, orders, brickwork_dynamics, tfim_quench (default all)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="seconds of Poisson arrivals per load point (300 for the 5-minute trace)")
+    ap.add_argument("--serve-fifo-seconds", type=float, default=None,
+                    help="replay only this many seconds of each trace in the one-launch-per-request arm")
     ap.add_argument("--serve-loads", default="0.25,0.5,0.75",
                     help="load points, as fractions of the capacity measured at N = 20")
     ap.add_argument("--batch-states", type=int, default=512)
@@ -246,13 +251,14 @@ def _pct(lat, q):
     return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None
 
 
-def run_serving(binding, torch, W, terms_per_s, seconds, loads, mode, chunk_terms=1 << 37):
+def run_serving(binding, torch, W, terms_per_s, seconds, loads, mode, chunk_terms=1 << 37, fifo_seconds=None):
     """Poisson arrivals at each of `loads` x measured capacity: through the
     server (slots with the autotuned two-pass plans of N = 17..20, large
     requests split into shift ranges of <= chunk_terms Pauli terms that take
     turns with the rest), and the same trace with one synchronous launch per
     request in arrival order (FIFO) on plans created and tuned before its
-    clock starts.  Both arms use the arithmetic mode `mode`."""
+    clock starts (on the first fifo_seconds of each trace, default all of
+    it).  Both arms use the arithmetic mode `mode`."""
     import threading as th
     ns, p = W.serving_n_distribution()
     mean_work = float(sum(pn * 4.0 ** n for n, pn in zip(ns, p)))
@@ -295,6 +301,9 @@ def run_serving(binding, torch, W, terms_per_s, seconds, loads, mode, chunk_term
                                             "states_per_s", "pauli_terms_per_s", "completed", "failed",
                                             "rejected", "peak_resident_bytes")}
         # one launch per request, FIFO, same arrivals
+        if fifo_seconds is not None:
+            trace = [r for r in trace if r[0] <= fifo_seconds]
+            res["fifo_seconds"] = fifo_seconds
         lat = []
         q, lock, done_ev = [], th.Lock(), th.Event()
 
@@ -719,41 +728,31 @@ def run_gpu(args):
 
     peaks, peak_src = load_peaks()
     extras = {}
-    if not args.no_extras:
-        try:
-            extras["serving"] = run_serving(binding, torch, W, value / world, args.serve_seconds,
-                                            [float(v) for v in args.serve_loads.split(",")], args.mode)
-        except Exception as exc:  # reported, not hidden
-            extras["serving"] = {"error": repr(exc)}
-        for bmode in ("fp32", "fp16_split"):
-            key = "batched" if bmode == "fp32" else f"batched_{bmode}"
+    want = set(args.extras.split(",")) if not args.no_extras else set()
+
+    def extra(name, fn):
+        if name in want or "all" in want:
             try:
-                extras[key] = run_batched(binding, torch, W, args.batch_states, bmode)
-            except Exception as exc:
-                extras[key] = {"error": repr(exc)}
-        try:
-            extras["fp64_check"] = run_fp64_check(binding, torch, W)
-        except Exception as exc:
-            extras["fp64_check"] = {"error": repr(exc)}
-        head = {"ms": statistics.mean(step_ms), "kernel_ms": statistics.mean(kern_ms), "kernel": kname,
-                "m2": m2_val, "tuning": tuning}
-        try:
-            extras["modes"] = run_modes(binding, torch, W, N, args.mode, head, peaks)
-        except Exception as exc:
-            extras["modes"] = {"error": repr(exc)}
-        try:
-            f32 = extras["modes"].get("fp32") or (head if args.mode == "fp32" else {})
-            extras["orders"] = run_orders(binding, torch, W, N, f32.get("kernel_ms"), f32.get("m2"))
-        except Exception as exc:
-            extras["orders"] = {"error": repr(exc)}
-        try:
-            extras["brickwork_dynamics"] = run_brickwork(binding, torch, W)
-        except Exception as exc:
-            extras["brickwork_dynamics"] = {"error": repr(exc)}
-        try:
-            extras["tfim_quench"] = run_tfim(binding, torch, W)
-        except Exception as exc:
-            extras["tfim_quench"] = {"error": repr(exc)}
+                extras[name] = fn()
+            except Exception as exc:  # reported, not hidden
+                extras[name] = {"error": repr(exc)}
+
+    head = {"ms": statistics.mean(step_ms), "kernel_ms": statistics.mean(kern_ms), "kernel": kname,
+            "m2": m2_val, "tuning": tuning}
+    extra("serving", lambda: run_serving(binding, torch, W, value / world, args.serve_seconds,
+                                         [float(v) for v in args.serve_loads.split(",")], args.mode,
+                                         fifo_seconds=args.serve_fifo_seconds))
+    extra("batched", lambda: run_batched(binding, torch, W, args.batch_states, "fp32"))
+    extra("batched_fp16_split", lambda: run_batched(binding, torch, W, args.batch_states, "fp16_split"))
+    extra("fp64_check", lambda: run_fp64_check(binding, torch, W))
+    extra("modes", lambda: run_modes(binding, torch, W, N, args.mode, head, peaks))
+
+    def orders():
+        f32 = (extras.get("modes") or {}).get("fp32") or (head if args.mode == "fp32" else {})
+        return run_orders(binding, torch, W, N, f32.get("kernel_ms"), f32.get("m2"))
+    extra("orders", orders)
+    extra("brickwork_dynamics", lambda: run_brickwork(binding, torch, W))
+    extra("tfim_quench", lambda: run_tfim(binding, torch, W))
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

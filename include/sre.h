@@ -333,9 +333,11 @@ SRE_API sre_status_t sre_m2_batched(sre_plan_t plan, const void *const *d_states
  *            expires (fixed limit of 5 s): the status the kernel records
  *            stays in the library's own array, out of the caller's reach.
  * Asynchronous on `stream`.  Its only scratch is one fixed module array of
- * about 5.4 MB that every GPU loading the library holds until exit; the
- * first call with a device current looks up that array's address and must
- * not be made during a stream capture.  Every call shares the array, so
+ * about 5.4 MB that every GPU loading the library holds until exit; a call
+ * made while `stream` is not being captured looks up that array's address
+ * (so a call after cudaDeviceReset finds the reloaded array), a call during
+ * a capture reuses the address found before, so the first call with a
+ * device current must not be made during a stream capture.  Every call shares the array, so
  * calls whose work overlaps on the GPU race; calls ordered on the GPU are
  * safe.  Returns SRE_EINVAL, SRE_EALIGN or SRE_ECUDA on error.
  */

@@ -20,8 +20,10 @@
 //
 // In host code the name g_noalloc_scratch stands for the device symbol, not
 // for a device address: the address is looked up with cudaGetSymbolAddress
-// on the first call made with a given device current, and that first call
-// must therefore not be made while a stream is being captured.
+// on every call made while its stream is not being captured (a
+// cudaDeviceReset unloads the module, and the array may come back
+// elsewhere); a call during a capture uses the address found before, so the
+// first call with a given device current must not be made during a capture.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -69,18 +71,26 @@ bool g_ready[kMaxDevices];
 unsigned char *g_base[kMaxDevices];
 sre::DeviceInfo g_info[kMaxDevices];
 
-// Once per device, with that device current: the device address of the
-// array and the device properties.
-sre_status_t setup(int dev) {
+// With the device current: the device address of the array and the device
+// properties.  The address is looked up again on every call made while
+// `stream` is not being captured (a cudaDeviceReset unloads the module, and
+// the array may come back elsewhere); during a capture the address found
+// before is used, and a capture before any lookup on the device fails.
+sre_status_t setup(int dev, cudaStream_t stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;  // unknown: do not look anything up
+    }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (g_ready[dev]) return SRE_OK;
+    if (cs != cudaStreamCaptureStatusNone) return g_ready[dev] ? SRE_OK : SRE_ECUDA;
     void *ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || !ptr) {
         cudaGetLastError();
         return SRE_ECUDA;
     }
-    if (sre::query_device(&g_info[dev]) != cudaSuccess) {
+    if (!g_ready[dev] && sre::query_device(&g_info[dev]) != cudaSuccess) {
         cudaGetLastError();
         return SRE_ECUDA;
     }
@@ -100,7 +110,7 @@ extern "C" sre_status_t sre_m2_noalloc(const void *d_state, int N, sre_stream_t 
         cudaGetLastError();
         return SRE_ECUDA;
     }
-    const sre_status_t s = setup(dev);
+    const sre_status_t s = setup(dev, (cudaStream_t)stream);
     if (s != SRE_OK) return s;
     unsigned char *base = g_base[dev];
 

@@ -72,3 +72,46 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     st = f(ctypes.c_void_p(psi.data_ptr()), 17, None, ctypes.c_void_p(out.data_ptr()))
     assert st == 1  # SRE_EINVAL: N above SRE_NOALLOC_MAX_QUBITS
+
+
+_RESET_CHILD = r"""
+import ctypes, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2512_24685_gb300 import binding, workloads as W
+lib = binding.load_library()
+rt_path = next(l.split()[-1] for l in open('/proc/self/maps') if 'libcudart' in l)
+rt = ctypes.CDLL(rt_path)
+f = lib.sre_m2_noalloc
+f.restype = ctypes.c_int
+f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+N = 14
+psi = W.haar_state(N, 4321, np.complex64)
+def once():
+    d_psi, d_out = ctypes.c_void_p(), ctypes.c_void_p()
+    assert rt.cudaMalloc(ctypes.byref(d_psi), ctypes.c_size_t(psi.nbytes)) == 0
+    assert rt.cudaMalloc(ctypes.byref(d_out), ctypes.c_size_t(8)) == 0
+    assert rt.cudaMemcpy(d_psi, psi.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(psi.nbytes), 1) == 0
+    assert f(d_psi, N, None, d_out) == 0
+    assert rt.cudaDeviceSynchronize() == 0
+    out = ctypes.c_double()
+    assert rt.cudaMemcpy(ctypes.byref(out), d_out, ctypes.c_size_t(8), 2) == 0
+    rt.cudaFree(d_psi); rt.cudaFree(d_out)
+    return out.value
+a = once()
+assert rt.cudaDeviceReset() == 0
+b = once()
+print(repr(a), repr(b))
+sys.exit(0 if a == b else 3)
+"""
+
+
+def test_noalloc_after_device_reset(env):
+    """A call after cudaDeviceReset (in a child process, which owns its own
+    context) finds the reloaded module array and gives the same M2."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _RESET_CHILD, root], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr[-2000:])

@@ -193,6 +193,7 @@ struct __align__(8) TcShared {
     unsigned long long s1_ring[8];  // pass-1 tile scale: (float bits, tile index + 1)
     uint32_t maxq[kCompWarps], maxp[kCompWarps];  // per block pair: max |psi|^2 of each warp's entries
     uint32_t maxt[2][kCompWarps];                  // BF16: per tile, max |value| of each warp
+    double epi_part[2][4];                         // pass-2 item partials of the epilogue warps
     uint32_t tmem;
 };
 
@@ -214,6 +215,7 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, const La
 }
 
 __device__ __forceinline__ void bar_sync_comp() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void bar_sync_epi() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 
 // Release / acquire at GPU scope by one lane for its warp: after __syncwarp
 // the fence also orders the other lanes' earlier accesses (fences are
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                     if (!x_valid(a, it.xc + (uint64_t)xl)) continue;
                     const int zb0 = (it.r & ((1 << ipx_log) - 1)) << a.G2_log;
                     const int y_hi = (int)((((size_t)it.slot * C + xl) * 2) << H2);
-                    wait_counter(a.done1 + it.chunk, (unsigned)(a.P1 * 4), a.status, a.wait_ns);
+                    wait_counter(a.done1 + it.chunk, (unsigned)a.P1, a.status, a.wait_ns);
                     // the chunk's scratch rows (generic stores of other CTAs,
                     // acquired above) come before the TMA reads
                     fence_proxy_async();
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
         uint32_t par_u = 0;             // parity of the next u_full1 (compute) / u_full2 (MMA) phase, per unit
         uint32_t par_d = 0;             // parity of the next d_full phase, per accumulator
         uint32_t mma_used = 0;          // MMA: accumulators committed to
+        unsigned long long p2items = 0;  // epilogue: pass-2 items done
         float2 Q[16];                   // compute: own factors of the block pair
         for (long long k = 0;; ++k) {
             const int qs = (int)(k % kQueue);
@@ -409,8 +412,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                 const int first = it.first, count = it.count;
                 if (count == 0) {
                     if (is_epi) {
-                        __syncwarp();
-                        if (lane == 0) {
+                        bar_sync_epi();
+                        if (warp == kEpiWarp0 && lane == 0) {
                             fence_acq_rel_gpu();
                             atomicAdd(a.done1 + it.chunk, 1u);
                         }
@@ -651,9 +654,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                             ++dtile;
                         }
                     }
-                    // the item's stores are complete: one arrival per epilogue warp
-                    __syncwarp();
-                    if (lane == 0) {
+                    // the item's stores are complete: after a barrier of the four
+                    // epilogue warps one release (fences are cumulative) and
+                    // one arrival per item
+                    bar_sync_epi();
+                    if (warp == kEpiWarp0 && lane == 0) {
                         fence_acq_rel_gpu();
                         atomicAdd(a.done1 + it.chunk, 1u);
                     }
@@ -752,23 +757,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ La
                     double acc = valid ? ldexp((double)part, 4 + 4 * (it.E - P)) : 0.0;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+                    // the four warps' partials, added in warp order by warp 8,
+                    // which releases the item with one arrival (the buffers
+                    // alternate between pass-2 items: warp 8 reads one before
+                    // it reaches the next item's barrier)
+                    const int pb = (int)(p2items & 1);
+                    ++p2items;
+                    if (lane == 0) sh.epi_part[pb][qd] = acc;
+                    bar_sync_epi();  // also orders every warp's discards before the arrival
+                    if (warp != kEpiWarp0) continue;
                     int last = 0;
-                    __syncwarp();  // the warp's discards precede its arrival
                     if (lane == 0) {
-                        a.item_part[(((size_t)it.slot * a.P2 + j) * 4) + qd] = acc;
+                        const double v = ((sh.epi_part[pb][0] + sh.epi_part[pb][1]) + sh.epi_part[pb][2]) +
+                                         sh.epi_part[pb][3];
+                        a.item_part[(size_t)it.slot * a.P2 + j] = v;
                         fence_acq_rel_gpu();
                         const unsigned old = atomicAdd(a.done2 + it.chunk, 1u);
-                        last = (old == (unsigned)(a.P2 * 4) - 1u);
+                        last = (old == (unsigned)a.P2 - 1u);
                     }
                     last = __shfl_sync(0xffffffffu, last, 0);
                     if (last) {
-                        // last warp of the chunk: per-shift and chunk
-                        // sums in fixed order, then release the slot
+                        // last item of the chunk: per-shift and chunk sums in
+                        // fixed order, then release the slot
                         fence_acq_rel_gpu();
-                        const int per_x_items = (1 << ipx_log) * 4;
+                        const int per_x_items = 1 << ipx_log;
                         double cs = 0.0;
                         for (int qq = 0; qq < C; ++qq) {
-                            const double *ip = a.item_part + ((size_t)it.slot * a.P2 + ((size_t)qq << ipx_log)) * 4;
+                            const double *ip = a.item_part + ((size_t)it.slot * a.P2 + ((size_t)qq << ipx_log));
                             double sx = 0.0;
                             for (int kk = lane; kk < per_x_items; kk += 32) sx += __ldcg(ip + kk);
 #pragma unroll

@@ -4,7 +4,9 @@ FP64 oracle's M2 per state (Eq. (final1), Algorithm 1's return value).
 
 tests/golden/n16_mix_oracle.json is written by
 tests/golden/make_n16_mix_oracle.py, which calls only the oracle; the states
-are regenerated here and their sha256 checked against the record first.
+are regenerated here and checked against the record's fingerprint (norm2 and
+eight amplitudes) within a rounding tolerance first: the generators' last bits
+differ between platforms, which moves M2 by far less than the tolerances.
 """
 import hashlib
 import json
@@ -45,8 +47,23 @@ def mix(dtype):
         pytest.skip(f"no complete {name} record")
     states = [psi for _, psi, _ in W.mixed_n16_batch(1, 16, 16, 8, dtype)]
     for psi, rec in zip(states, recs):
-        assert hashlib.sha256(psi.tobytes()).hexdigest() == rec["sha256"], "generator drifted from the record"
+        assert_fingerprint(psi, rec)
     return states, [r["m2"] for r in recs], [r["kind"] for r in recs]
+
+
+PROBE = [0, 1, 2, 3, 4097, 20000, 32768, 65535]
+
+
+def assert_fingerprint(psi, rec):
+    """The regenerated state equals the recorded one up to rounding."""
+    if hashlib.sha256(psi.tobytes()).hexdigest() == rec["sha256"]:
+        return
+    rtol = 1e-6 if psi.dtype == np.complex64 else 1e-12
+    v = psi.astype(np.complex128)
+    n2 = float(np.sum(v.real ** 2 + v.imag ** 2))
+    assert abs(n2 - rec["norm2"]) <= rtol * rec["norm2"], "generator drifted from the record"
+    for i, (re, im) in zip(PROBE, rec["probe"]):
+        assert abs(v[i] - complex(re, im)) <= rtol * (1e-3 + abs(complex(re, im))), ("generator drifted", i)
 
 
 @pytest.mark.parametrize("mode", ["fp32", "fp16_split", "bf16_split"])

@@ -207,8 +207,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"N={N} Haar-random state, all 4^{N} Pauli strings (bounded shift sample per step)",
-                   "N": N},
+        "config": {"workload": f"N={N} Haar-random state (complex64), all 4^{N} Pauli strings per step",
+                   "N": N, "states_per_gpu": 1, "parallelism": f"replicas x{args.gpus}",
+                   "sample": "each step evaluates a bounded range of shifts (see cpu_baseline.sample); "
+                             "the throughput is Pauli terms of that range per second"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

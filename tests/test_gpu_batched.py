@@ -167,3 +167,20 @@ def test_split_mode_batch(sre, torch_cuda, mode):
         assert r == g
         if v.size <= 1 << 16:
             assert abs(g - oracle.m2(v)) <= 1e-6, (v.size, g)
+
+
+def test_split_mode_batch_converted(sre, torch_cuda):
+    """complex128 states batched in the FP16 split mode (converted to
+    complex64 on the device, then the tensor-core kernel for N = 16, 17):
+    each equals its single evaluation in that mode bit for bit."""
+    torch = torch_cuda
+    spec = [(16, 6, 41), (13, 3, 42), (17, 9, 43)]
+    states = mixed_states(spec, np.complex128)
+    ts = [dev(torch, v) for v in states]
+    with sre.Plan(17, "c128", "fp16_split") as p:
+        got = p.m2_batched(ts).cpu().numpy()
+        singles = [p.m2(t) for t in ts]
+    for v, g, s in zip(states, got, singles):
+        assert g == s, (v.size, g, s)
+        if v.size <= 1 << 13:
+            assert abs(g - oracle.m2(v)) <= 1e-6

@@ -204,3 +204,23 @@ def test_server_split_mode(sre, torch_cuda):
     for g, w in zip(got, want):
         assert abs(g - w) <= 1e-12, (g, w)
     assert abs(got[1] - oracle.m2(states[1])) <= 1e-6
+
+
+def test_server_split_mode_chunked(sre, torch_cuda):
+    """The bench's serving configuration: FP16 split server, requests with
+    N > 16 split into shift ranges; each result matches the state's single
+    evaluation in that mode (range partial sums added in order: 1e-9)."""
+    torch = torch_cuda
+    states = [W.haar_state(18, 821, np.complex64), W.haar_state(12, 822, np.complex64),
+              W.brickwork_state(17, 10, 823, np.complex64), W.haar_state(18, 824, np.complex64)]
+    want = []
+    for v in states:
+        n = v.size.bit_length() - 1
+        with sre.Plan(n, "c64", "fp16_split" if n > 16 else "fp32") as p:
+            want.append(p.m2(torch.from_numpy(v).cuda()))
+    with sre.Server(max_inflight=3, max_N=18, mode="fp16_split", chunk_terms=1 << 33) as srv:
+        got = [srv.wait(t, 120000) for t in [srv.submit(v) for v in states]]
+        st = srv.stats()
+    for g, w in zip(got, want):
+        assert abs(g - w) <= 1e-9, (g, w)
+    assert st["completed"] == len(states) and st["failed"] == 0

@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
                         bulk_load(smem_u32(par), psi + (((uint64_t)th ^ xh) << kTileBits), kStageBytes, mb);
                     };
                     if (tid == 0) {
-                        fence_proxy_async();
+                        // the stage's earlier readers (generic loads) before the copies' writes
+                        fence_proxy_async_smem();
                         issue_pair(0);
                     }
                     const int xlow = xl0;
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
                         for (int i = 0; i < 16; ++i) v[i] = Cx<R>::from(own[elem<1>(tid, i)]);
                         __syncthreads();  // both stage buffers are free
                         if (tid == 0 && kb + 1 < nb) {
-                            fence_proxy_async();
+                            fence_proxy_async_smem();
                             issue_pair(kb + 1);
                         }
                         reg_stages<1, 12, R>(v);
@@ -396,7 +397,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_large(cons
                         if (gb + 2 < ntiles) {
                             __syncthreads();  // every thread has read stage st
                             if (tid == 0) {
-                                fence_proxy_async();
+                                // shared-memory WAR only: the scratch rows were
+                                // ordered before the copies once per item above
+                                fence_proxy_async_smem();
                                 issue(gb + 2, st);
                             }
                         }

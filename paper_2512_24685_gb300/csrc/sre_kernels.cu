@@ -603,9 +603,9 @@ static cudaError_t enqueue_m2_t(const Workspace &ws, const DeviceInfo &dev, cons
 // M2 of one complex64 state in FP32 with fixed two-pass configurations for
 // both shift ranges (no allocation, no autotuning): used by callers that
 // hand in preassigned scratch.  It shares the norm and finalize kernels
-// with the single-state path, but runs the two-pass kernel with the given
-// fixed configuration for every N > 12: no single-pass kernel for
-// N = 13..15 and no autotuned plan.
+// with the single-state path and, like it, takes the single-pass kernel for
+// the shift ranges of N = 13..15; larger N run the two-pass kernel with the
+// given fixed configuration (no autotuned plan).
 cudaError_t enqueue_m2_fixed(const Workspace &ws, const DeviceInfo &dev, const void *psi, int N,
                              const LargeCfg &cfg_full, const LargeCfg &cfg_half, cudaStream_t st,
                              double *d_m2, long long wait_ns) {
@@ -631,6 +631,18 @@ cudaError_t enqueue_m2_fixed(const Workspace &ws, const DeviceInfo &dev, const v
         size_t chunks = 0;
         for (int half = 0; half <= 1; ++half) {
             const uint64_t xb = half ? (uint64_t)kTile : 0, xe = half ? d : (uint64_t)kTile;
+            if (mid_applies(N, half, 8)) {
+                // one, two or four blocks per shift: the single-pass kernel,
+                // one partial per shift, no ring and no waits
+                const long long ns = (long long)(xe - xb);
+                if (chunks + (size_t)ns > ws.chunk_cap) return cudaErrorInvalidValue;
+                if ((e = launch_mid<R>(N, half, psi, nullptr, 1, ns, xb, 2, ws.chunk_sum + chunks, nullptr, dev,
+                                       st)) != cudaSuccess)
+                    return e;
+                chunks += (size_t)ns;
+                if (!half) seg1 = (long long)chunks;
+                continue;
+            }
             LargeArgs a;
             int grid = 0;
             if ((e = make_large_args(&a, ws, dev, psi, N, xb, xe, half, 8, chunks, nullptr, wait_ns,

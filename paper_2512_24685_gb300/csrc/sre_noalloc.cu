@@ -35,7 +35,8 @@ namespace {
 
 constexpr int kNoAllocMaxN = SRE_NOALLOC_MAX_QUBITS;  // 16
 
-// Fixed two-pass configuration: one shift per chunk, 8 ring slots, lag 3.
+// Fixed two-pass configuration (N = 16; N = 13..15 take the single-pass
+// kernel): one shift per chunk, 8 ring slots, lag 3.
 constexpr int kRingSlots = 8;
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }

@@ -551,6 +551,8 @@ def run_tfim(binding, torch, W, cases=((14, 100, 10), (16, 100, 3)), dt=0.2):
 # evaluation.  Valid only for that kernel build and tuning; any other run
 # reports null.
 TRAFFIC = {
+    # FP32 CUDA-core two-pass kernel, its autotuned tuning (read + written on the slice)
+    ("fp32", (0, 47, 23, 3, 3)): 45.449725e9 + 61.593259e9,
     # tensor-core kernel, FP16 pieces, the tunings its autotuner picks
     # (read + written on the slice)
     ("fp16_split", (3, 6, 2, 4, 0)): 45.709644e9 + 59.002857e9,

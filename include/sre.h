@@ -310,7 +310,11 @@ SRE_API sre_status_t sre_m_alpha_from_sums(const double *d_S, const double *d_n2
  * d_states: host array of `count`
  * device pointers; Ns: host array of the N_i; d_m2_out: device array of
  * `count` doubles (NaN for a zero / non-finite state, and for every state
- * of a submission in which a device wait expired).  The batch is
+ * of a submission in which a device wait expired).  In the split modes the
+ * states with 16 <= N <= 20 (all of a size class 16-byte aligned) take the
+ * tensor-core kernel for their halved shifts, each with its own scale
+ * table; every result equals the state's sre_m2 in the plan's mode bit for
+ * bit.  The batch is
  * executed by persistent kernels walking one work list, and is replayed
  * from a captured CUDA graph when the same (pointers, Ns) batch is
  * submitted again.  Asynchronous.  Errors: SRE_EINVAL, SRE_EALIGN,

@@ -26,7 +26,8 @@
 //     (hi, lo) of scratch rows [slot][shift][plane][t'_h][8192].
 // pass 2, per tile of 128 scratch rows x 32 complex columns:
 //   * TMA copies the hi and lo planes into the two 64-column atom columns of
-//     an N = 128 B operand (128-byte swizzle); three stages in flight;
+//     an N = 128 B operand (128-byte swizzle), through the ring of four
+//     copy units that pass 1's block pairs also use;
 //   * one MMA stage D = A B over the h2 high bits, A = H_128 (h2 = 7) or the
 //     block-diagonal I (x) H_{2^h2} (h2 < 7, the tile then stacks 2^(7-h2)
 //     column blocks along K);
@@ -38,7 +39,7 @@
 // largest such product over the shift's blocks, times 1 + 2^-10) keeps every
 // scaled value inside [-2^P, 2^P]: pass 2 contracts over rows that come from
 // different blocks and needs one scale along K.  k_tc_scales computes E per
-// x >> 12 before the launch.
+// x >> 12 (per state, for the states of a batch class) before the launch.
 //
 // Pipelining: warp-specialized roles (below) with two B buffers, three TMEM
 // accumulators and a ring of copy units, so that copies, MMAs and CUDA-core
